@@ -1,0 +1,206 @@
+"""FP64 CPU oracle for the CETRA transit search (Smith et al. 2025, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY. This package is imported by the test suite, by the
+smoke check of the build entry point and by the benchmark's CPU-baseline leg,
+and by nothing else. The product (the CUDA library and its Python binding)
+never imports, links or calls it, and the two share no code.
+
+The arithmetic lives in ``cetra_oracle.c`` (plain C, FP64, OpenMP over
+independent windows / periods); this module only builds it and marshals numpy
+arrays through ctypes. Each C function cites the passage of the paper it
+follows and lists the readings taken where the paper is silent.
+
+Parity status: every step is pinned by the CPU tests in
+``tests/test_oracle_pins.py`` (closed forms, noiseless injections, brute-force
+likelihood maximisation, invariants, the paper's toy example); the only
+conventions that no external fact fixes are the readings R1, R3, R5, R6 and R7
+listed in the C file, which are choices rather than results.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cetra_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to the source (gcc, FP64, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           _SRC, "-o", _LIB + ".tmp", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [
+        ("t_ref", ctypes.c_double),
+        ("cadence", ctypes.c_double),
+        ("t0_step", ctypes.c_double),
+        ("p", ctypes.c_int64),
+        ("q", ctypes.c_int64),
+        ("n_pad", ctypes.c_int64),
+        ("n_grid", ctypes.c_int64),
+        ("n_t0", ctypes.c_int64),
+        ("n_kept", ctypes.c_int64),
+        ("tau_max", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    lib.oracle_geometry.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    P, ctypes.c_int, ctypes.POINTER(_Geom)]
+    lib.oracle_resample.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.POINTER(_Geom), P, P]
+    lib.oracle_template.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
+    lib.oracle_linear.argtypes = [ctypes.POINTER(_Geom), P, P, P, ctypes.c_int, P, ctypes.c_int,
+                                  P, P, P, P]
+    lib.oracle_periodic.argtypes = [ctypes.POINTER(_Geom), P, ctypes.c_int, P, P, P, P,
+                                    ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.oracle_logl0.argtypes = [ctypes.POINTER(_Geom), P, P]
+    lib.oracle_logl0.restype = ctypes.c_double
+    lib.oracle_num_threads.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with status {rc}")
+
+
+@dataclass
+class Geometry:
+    t_ref: float
+    cadence: float
+    t0_step: float
+    p: int
+    q: int
+    n_pad: int
+    n_grid: int
+    n_t0: int
+    n_kept: int
+    tau_max: float
+    _raw: _Geom = None
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def geometry(time, flux, flux_err, durations, cadence=0.0, t0_step=0.0) -> Geometry:
+    lib = _load()
+    t = np.ascontiguousarray(time, np.float64)
+    f = np.ascontiguousarray(flux, np.float32)
+    e = np.ascontiguousarray(flux_err, np.float32)
+    d = np.ascontiguousarray(durations, np.float64)
+    g = _Geom()
+    _check(lib.oracle_geometry(_ptr(t), _ptr(f), _ptr(e), t.size, float(cadence), float(t0_step),
+                               _ptr(d), d.size, ctypes.byref(g)), "geometry")
+    return Geometry(g.t_ref, g.cadence, g.t0_step, g.p, g.q, g.n_pad, g.n_grid, g.n_t0,
+                    g.n_kept, g.tau_max, g)
+
+
+def resample(time, flux, flux_err, geom: Geometry, flux_is_offset=False):
+    lib = _load()
+    t = np.ascontiguousarray(time, np.float64)
+    f = np.ascontiguousarray(flux, np.float32)
+    e = np.ascontiguousarray(flux_err, np.float32)
+    y = np.empty(geom.n_grid, np.float64)
+    w = np.empty(geom.n_grid, np.float64)
+    _check(lib.oracle_resample(_ptr(t), _ptr(f), _ptr(e), t.size, int(bool(flux_is_offset)),
+                               ctypes.byref(geom._raw), _ptr(y), _ptr(w)), "resample")
+    return y, w
+
+
+def template(tmpl, L=1024):
+    lib = _load()
+    tm = np.ascontiguousarray(tmpl, np.float32)
+    out = np.empty(int(L), np.float64)
+    _check(lib.oracle_template(_ptr(tm), tm.size, int(L), _ptr(out)), "template")
+    return out
+
+
+def linear(geom: Geometry, y_grid, w_grid, durations, T, with_kappa=False):
+    """Linear search (Sec. 2.2). Returns depth, depth_var, LR (and kappa), each [J][I]."""
+    lib = _load()
+    y = np.ascontiguousarray(y_grid, np.float64)
+    w = np.ascontiguousarray(w_grid, np.float64)
+    d = np.ascontiguousarray(durations, np.float64)
+    Tm = np.ascontiguousarray(T, np.float64)
+    J, I = d.size, geom.n_t0
+    dep = np.empty((J, I), np.float64)
+    var = np.empty((J, I), np.float64)
+    lr = np.empty((J, I), np.float64)
+    kap = np.empty((J, I), np.float64) if with_kappa else None
+    _check(lib.oracle_linear(ctypes.byref(geom._raw), _ptr(y), _ptr(w), _ptr(d), J, _ptr(Tm),
+                             Tm.size, _ptr(dep), _ptr(var), _ptr(lr), _ptr(kap)), "linear")
+    if with_kappa:
+        return dep, var, lr, kap
+    return dep, var, lr
+
+
+def periodic(geom: Geometry, durations, depth, depth_var, lr, periods, mask=None):
+    """Periodic search (Sec. 2.3). Returns a dict of per-period arrays."""
+    lib = _load()
+    d = np.ascontiguousarray(durations, np.float64)
+    P = np.ascontiguousarray(periods, np.float64)
+    dep = np.ascontiguousarray(depth, np.float64)
+    var = np.ascontiguousarray(depth_var, np.float64)
+    l = np.ascontiguousarray(lr, np.float64)
+    m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+    K = P.size
+    out = {k: np.empty(K, np.float64) for k in ("dlogl", "t0", "duration", "depth", "depth_var")}
+    out["i"] = np.empty(K, np.int64)
+    out["j"] = np.empty(K, np.int32)
+    _check(lib.oracle_periodic(ctypes.byref(geom._raw), _ptr(d), d.size, _ptr(dep), _ptr(var),
+                               _ptr(l), _ptr(P), K, _ptr(m), _ptr(out["dlogl"]), _ptr(out["t0"]),
+                               _ptr(out["duration"]), _ptr(out["depth"]),
+                               _ptr(out["depth_var"]), _ptr(out["i"]), _ptr(out["j"])),
+           "periodic")
+    return out
+
+
+def logl0(geom: Geometry, y_grid, w_grid) -> float:
+    lib = _load()
+    y = np.ascontiguousarray(y_grid, np.float64)
+    w = np.ascontiguousarray(w_grid, np.float64)
+    return float(lib.oracle_logl0(ctypes.byref(geom._raw), _ptr(y), _ptr(w)))
+
+
+def search(time, flux, flux_err, durations, tmpl, periods=None, *, cadence=0.0, t0_step=0.0,
+           L=1024, flux_is_offset=False, mask=None, with_kappa=False):
+    """Whole pipeline: geometry, resample, template, linear search and (optionally) periodic."""
+    g = geometry(time, flux, flux_err, durations, cadence, t0_step)
+    y, w = resample(time, flux, flux_err, g, flux_is_offset)
+    T = template(tmpl, L)
+    lin = linear(g, y, w, durations, T, with_kappa=with_kappa)
+    res = {"geom": g, "y_grid": y, "w_grid": w, "T": T, "depth": lin[0], "depth_var": lin[1],
+           "dlogl": lin[2]}
+    if with_kappa:
+        res["kappa"] = lin[3]
+    res["logl0"] = logl0(g, y, w)
+    if periods is not None:
+        res["periodic"] = periodic(g, durations, lin[0], lin[1], lin[2], periods, mask)
+    return res
