@@ -38,6 +38,9 @@
  *       Null cells are skipped by the fold; a period with no valid cell is null.
  *   R11 Ties in the per-period maximum go to the smallest duration index j,
  *       then the smallest t0 index i.
+ *   R12 A period shorter than one t0 step (P/s < 1) has no distinct phase and
+ *       would fold one window onto itself; such a period (and a non-finite
+ *       one) is null.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (R8 needs
  * -ffp-contract=off: aarch64 compilers contract a*b+c into fma by default).
@@ -328,7 +331,8 @@ int oracle_periodic(const oracle_geom *g, const double *durations, int n_dur,
         double best = -INFINITY, best_z = NAN, best_v = NAN;
         int64_t best_i = -1;
         int best_j = -1;
-        for (int j = 0; j < n_dur; j++) {
+        int valid = Ps >= 1.0 && isfinite(Ps); /* R12 */
+        for (int j = 0; valid && j < n_dur; j++) {
             if (!(durations[j] < P)) continue;
             if (mask && !mask[(int64_t)k * n_dur + j]) continue;
             const double *dep = depth + (int64_t)j * I;

@@ -338,6 +338,16 @@ def test_phases_extend_to_ceil_of_period():
     assert r["periodic"]["i"][0] == 20
 
 
+def test_period_shorter_than_t0_step_is_null():
+    """R12: P < s folds a window onto itself; such periods are null."""
+    t, f, e = _curve(16, n=200)
+    r = run(t, f, e, [0.3 * C_EXACT], box_template(), [0.5 * C_EXACT, 3.0 * C_EXACT],
+            cadence=C_EXACT, t0_step=C_EXACT)
+    per = r["periodic"]
+    assert np.isnan(per["dlogl"][0]) and per["i"][0] == -1 and per["j"][0] == -1
+    assert not np.isnan(per["dlogl"][1])
+
+
 def test_single_epoch_fold_equals_linear():
     """P longer than the t0 grid: every phase has one epoch, so the per-period
     maximum is the linear-search maximum over i < ceil(P/s) (P4)."""
