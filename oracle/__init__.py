@@ -74,6 +74,10 @@ def _load():
                                   P, P, P, P]
     lib.oracle_periodic.argtypes = [ctypes.POINTER(_Geom), P, ctypes.c_int, P, P, P, P,
                                     ctypes.c_int, P, P, P, P, P, P, P, P]
+    lib.oracle_linear_cells.argtypes = [ctypes.POINTER(_Geom), P, P, P, ctypes.c_int, P,
+                                        ctypes.c_int, ctypes.c_int64, P, P, P, P, P, P]
+    lib.oracle_periodic_at.argtypes = [ctypes.POINTER(_Geom), ctypes.c_int, P, P, P, P,
+                                       ctypes.c_int, P, P, P, P, P]
     lib.oracle_logl0.argtypes = [ctypes.POINTER(_Geom), P, P]
     lib.oracle_logl0.restype = ctypes.c_double
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -159,6 +163,39 @@ def linear(geom: Geometry, y_grid, w_grid, durations, T, with_kappa=False):
     if with_kappa:
         return dep, var, lr, kap
     return dep, var, lr
+
+
+def linear_cells(geom: Geometry, y_grid, w_grid, durations, T, j, i):
+    """Linear search at the cells (j[c], i[c]) only. Returns depth, depth_var, LR, kappa."""
+    lib = _load()
+    y = np.ascontiguousarray(y_grid, np.float64)
+    w = np.ascontiguousarray(w_grid, np.float64)
+    d = np.ascontiguousarray(durations, np.float64)
+    Tm = np.ascontiguousarray(T, np.float64)
+    jj = np.ascontiguousarray(j, np.int32)
+    ii = np.ascontiguousarray(i, np.int64)
+    n = jj.size
+    out = [np.empty(n, np.float64) for _ in range(4)]
+    _check(lib.oracle_linear_cells(ctypes.byref(geom._raw), _ptr(y), _ptr(w), _ptr(d), d.size,
+                                   _ptr(Tm), Tm.size, n, _ptr(jj), _ptr(ii), *[_ptr(o) for o in out]),
+           "linear_cells")
+    return tuple(out)
+
+
+def periodic_at(geom: Geometry, depth, depth_var, lr, periods, i_at, j_at):
+    """Eq. 4 at (i_at[k], j_at[k]) for each period k. Returns LR, Z, var_Z."""
+    lib = _load()
+    dep = np.ascontiguousarray(depth, np.float64)
+    var = np.ascontiguousarray(depth_var, np.float64)
+    l = np.ascontiguousarray(lr, np.float64)
+    P = np.ascontiguousarray(periods, np.float64)
+    ii = np.ascontiguousarray(i_at, np.int64)
+    jj = np.ascontiguousarray(j_at, np.int32)
+    out = [np.empty(P.size, np.float64) for _ in range(3)]
+    _check(lib.oracle_periodic_at(ctypes.byref(geom._raw), dep.shape[0], _ptr(dep), _ptr(var),
+                                  _ptr(l), _ptr(P), P.size, _ptr(ii), _ptr(jj),
+                                  *[_ptr(o) for o in out]), "periodic_at")
+    return tuple(out)
 
 
 def periodic(geom: Geometry, durations, depth, depth_var, lr, periods, mask=None):

@@ -252,53 +252,75 @@ static double window_x(int64_t n, int64_t i, int64_t p, int64_t q, double Dt) {
  * sum_n |m_n W_n y_n| over the window, the condition number of A = sum m W y
  * used to bound FP32 cancellation in the tests.
  */
+static void linear_cell(const oracle_geom *g, const double *y_grid, const double *w_grid,
+                        double D, const double *T, int L, int64_t i,
+                        double *depth, double *depth_var, double *lr, double *kappa) {
+    const int64_t Ng = g->n_grid, p = g->p, q = g->q;
+    double Dt = (D * (double)q) / g->cadence;
+    /* candidate grid points (a superset of the window; membership is decided by x) */
+    int64_t lo = (int64_t)floor(((double)(i * p) - 0.5 * Dt) / (double)q) - 1;
+    int64_t hi = (int64_t)ceil(((double)(i * p) + 0.5 * Dt) / (double)q) + 1;
+    if (lo < 0) lo = 0;
+    if (hi > Ng - 1) hi = Ng - 1;
+    double sw = 0.0, swd = 0.0, kap = 0.0;
+    for (int64_t n = lo; n <= hi; n++) {
+        double x = window_x(n, i, p, q, Dt);
+        if (!(x >= 0.0 && x <= 1.0) || !(w_grid[n] > 0.0)) continue;
+        int64_t l = (int64_t)floor(x * (double)(L - 1) + 0.5);
+        double m = T[l];
+        kap += fabs(m * w_grid[n] * y_grid[n]);
+        if (m == 0.0) continue;
+        double dn = y_grid[n] / m;
+        double wt = m * m * w_grid[n];
+        sw += wt;
+        swd += wt * dn;
+    }
+    if (kappa) *kappa = kap;
+    if (!(sw > 0.0)) {
+        *depth = NAN; *depth_var = NAN; *lr = NAN;
+        return;
+    }
+    double dep = swd / sw;
+    double r = 0.0;
+    for (int64_t n = lo; n <= hi; n++) {
+        double x = window_x(n, i, p, q, Dt);
+        if (!(x >= 0.0 && x <= 1.0) || !(w_grid[n] > 0.0)) continue;
+        int64_t l = (int64_t)floor(x * (double)(L - 1) + 0.5);
+        double m = T[l];
+        double res = dep * m - y_grid[n];
+        r += w_grid[n] * (-0.5 * res * res + 0.5 * y_grid[n] * y_grid[n]);
+    }
+    *depth = dep;
+    *depth_var = 1.0 / sw;
+    *lr = r;
+}
+
 int oracle_linear(const oracle_geom *g, const double *y_grid, const double *w_grid,
                   const double *durations, int n_dur, const double *T, int L,
                   double *depth, double *depth_var, double *lr, double *kappa) {
-    const int64_t I = g->n_t0, Ng = g->n_grid, p = g->p, q = g->q;
+    const int64_t I = g->n_t0;
     const int64_t total = (int64_t)n_dur * I;
     #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t ji = 0; ji < total; ji++) {
         int j = (int)(ji / I);
         int64_t i = ji % I;
-        double Dt = (durations[j] * (double)q) / g->cadence;
-        /* candidate grid points (a superset of the window; membership is decided by x) */
-        int64_t lo = (int64_t)floor(((double)(i * p) - 0.5 * Dt) / (double)q) - 1;
-        int64_t hi = (int64_t)ceil(((double)(i * p) + 0.5 * Dt) / (double)q) + 1;
-        if (lo < 0) lo = 0;
-        if (hi > Ng - 1) hi = Ng - 1;
-        double sw = 0.0, swd = 0.0, kap = 0.0;
-        for (int64_t n = lo; n <= hi; n++) {
-            double x = window_x(n, i, p, q, Dt);
-            if (!(x >= 0.0 && x <= 1.0) || !(w_grid[n] > 0.0)) continue;
-            int64_t l = (int64_t)floor(x * (double)(L - 1) + 0.5);
-            double m = T[l];
-            kap += fabs(m * w_grid[n] * y_grid[n]);
-            if (m == 0.0) continue;
-            double dn = y_grid[n] / m;
-            double wt = m * m * w_grid[n];
-            sw += wt;
-            swd += wt * dn;
-        }
-        if (kappa) kappa[ji] = kap;
-        if (!(sw > 0.0)) {
-            depth[ji] = NAN; depth_var[ji] = NAN; lr[ji] = NAN;
-            continue;
-        }
-        double dep = swd / sw;
-        double r = 0.0;
-        for (int64_t n = lo; n <= hi; n++) {
-            double x = window_x(n, i, p, q, Dt);
-            if (!(x >= 0.0 && x <= 1.0) || !(w_grid[n] > 0.0)) continue;
-            int64_t l = (int64_t)floor(x * (double)(L - 1) + 0.5);
-            double m = T[l];
-            double res = dep * m - y_grid[n];
-            r += w_grid[n] * (-0.5 * res * res + 0.5 * y_grid[n] * y_grid[n]);
-        }
-        depth[ji] = dep;
-        depth_var[ji] = 1.0 / sw;
-        lr[ji] = r;
+        linear_cell(g, y_grid, w_grid, durations[j], T, L, i, &depth[ji], &depth_var[ji],
+                    &lr[ji], kappa ? &kappa[ji] : NULL);
     }
+    return ORACLE_OK;
+}
+
+/* The same linear search evaluated only at the n_cells cells (j[c], i[c]). */
+int oracle_linear_cells(const oracle_geom *g, const double *y_grid, const double *w_grid,
+                        const double *durations, int n_dur, const double *T, int L,
+                        int64_t n_cells, const int32_t *j, const int64_t *i,
+                        double *depth, double *depth_var, double *lr, double *kappa) {
+    for (int64_t c = 0; c < n_cells; c++)
+        if (j[c] < 0 || j[c] >= n_dur || i[c] < 0 || i[c] >= g->n_t0) return ORACLE_EINVAL;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < n_cells; c++)
+        linear_cell(g, y_grid, w_grid, durations[j[c]], T, L, i[c], &depth[c], &depth_var[c],
+                    &lr[c], kappa ? &kappa[c] : NULL);
     return ORACLE_OK;
 }
 
@@ -316,6 +338,39 @@ int oracle_linear(const oracle_geom *g, const double *y_grid, const double *w_gr
  * Outputs per period: LR, t0 (absolute days, mid-time), D, Z, var_Z and the
  * winning (i, j); NaN and -1 for a period with no valid cell.
  */
+/* Eq. 3 / Eq. 4 at one (t_i, D_j, P_k); returns 0 when no epoch cell is valid. */
+static int fold_cell(int64_t I, const double *dep, const double *var, const double *lrj,
+                     double Ps, int64_t i, double *lr_out, double *z_out, double *zvar_out) {
+    double sw = 0.0, swd = 0.0;
+    int any = 0;
+    for (int64_t e = 0;; e++) {
+        int64_t cell = i + (int64_t)floor((double)e * Ps + 0.5);
+        if (cell >= I) break;
+        if (isnan(lrj[cell])) continue;
+        sw += 1.0 / var[cell];
+        swd += dep[cell] / var[cell];
+        any = 1;
+    }
+    if (!any) return 0;
+    double Z = swd / sw;
+    double L = 0.0;
+    for (int64_t e = 0;; e++) {
+        int64_t cell = i + (int64_t)floor((double)e * Ps + 0.5);
+        if (cell >= I) break;
+        if (isnan(lrj[cell])) continue;
+        double dz = dep[cell] - Z;
+        L += lrj[cell] - 0.5 * dz * dz / var[cell];
+    }
+    *lr_out = L;
+    *z_out = Z;
+    *zvar_out = 1.0 / sw;
+    return 1;
+}
+
+static double period_steps(const oracle_geom *g, double P) {
+    return (P * (double)g->q) / (g->cadence * (double)g->p);
+}
+
 int oracle_periodic(const oracle_geom *g, const double *durations, int n_dur,
                     const double *depth, const double *depth_var, const double *lr,
                     const double *periods, int n_per, const uint8_t *mask,
@@ -325,7 +380,7 @@ int oracle_periodic(const oracle_geom *g, const double *durations, int n_dur,
     #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < n_per; k++) {
         double P = periods[k];
-        double Ps = (P * (double)q) / (g->cadence * (double)p);
+        double Ps = period_steps(g, P);
         double cph = ceil(Ps);
         int64_t nph = (cph < (double)I) ? (int64_t)cph : I;
         double best = -INFINITY, best_z = NAN, best_v = NAN;
@@ -339,28 +394,10 @@ int oracle_periodic(const oracle_geom *g, const double *durations, int n_dur,
             const double *var = depth_var + (int64_t)j * I;
             const double *lrj = lr + (int64_t)j * I;
             for (int64_t i = 0; i < nph; i++) {
-                double sw = 0.0, swd = 0.0;
-                int any = 0;
-                for (int64_t e = 0;; e++) {
-                    int64_t cell = i + (int64_t)floor((double)e * Ps + 0.5);
-                    if (cell >= I) break;
-                    if (isnan(lrj[cell])) continue;
-                    sw += 1.0 / var[cell];
-                    swd += dep[cell] / var[cell];
-                    any = 1;
-                }
-                if (!any) continue;
-                double Z = swd / sw;
-                double L = 0.0;
-                for (int64_t e = 0;; e++) {
-                    int64_t cell = i + (int64_t)floor((double)e * Ps + 0.5);
-                    if (cell >= I) break;
-                    if (isnan(lrj[cell])) continue;
-                    double dz = dep[cell] - Z;
-                    L += lrj[cell] - 0.5 * dz * dz / var[cell];
-                }
+                double L, Z, V;
+                if (!fold_cell(I, dep, var, lrj, Ps, i, &L, &Z, &V)) continue;
                 if (L > best) {
-                    best = L; best_z = Z; best_v = 1.0 / sw; best_i = i; best_j = j;
+                    best = L; best_z = Z; best_v = V; best_i = i; best_j = j;
                 }
             }
         }
@@ -376,6 +413,28 @@ int oracle_periodic(const oracle_geom *g, const double *durations, int n_dur,
             zvar_out[k] = best_v;
             i_out[k] = best_i;
             j_out[k] = best_j;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* The periodic likelihood of Eq. 4 at the given (i[k], j[k]) of each period k
+ * (NaN where no epoch cell is valid or the cell is out of range). */
+int oracle_periodic_at(const oracle_geom *g, int n_dur, const double *depth,
+                       const double *depth_var, const double *lr, const double *periods,
+                       int n_per, const int64_t *i_at, const int32_t *j_at,
+                       double *lr_out, double *z_out, double *zvar_out) {
+    const int64_t I = g->n_t0;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < n_per; k++) {
+        lr_out[k] = NAN; z_out[k] = NAN; zvar_out[k] = NAN;
+        if (j_at[k] < 0 || j_at[k] >= n_dur || i_at[k] < 0 || i_at[k] >= I) continue;
+        double Ps = period_steps(g, periods[k]);
+        if (!(Ps >= 1.0) || !isfinite(Ps)) continue;
+        int64_t o = (int64_t)j_at[k] * I;
+        double L, Z, V;
+        if (fold_cell(I, depth + o, depth_var + o, lr + o, Ps, i_at[k], &L, &Z, &V)) {
+            lr_out[k] = L; z_out[k] = Z; zvar_out[k] = V;
         }
     }
     return ORACLE_OK;

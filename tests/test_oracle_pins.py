@@ -508,3 +508,25 @@ def test_toy_example_of_figures_2_and_3():
         near = np.abs(periods - alias) <= 0.01 * alias
         assert per[near].max() < per[kbest]
         assert per[near].max() > np.median(per)
+
+
+def test_cell_evaluators_agree_with_full_search():
+    """The per-cell entry points (used for sampled parity at full sizes and for
+    epsilon-tie checks) return exactly what the full search computes."""
+    t, f, e = _curve(17, n=700)
+    durs = np.array([3.0, 8.0, 13.0]) * C_EXACT
+    P = synth.log_grid(20 * C_EXACT, 300 * C_EXACT, 30)
+    r = run(t, f, e, durs, synth.default_template(), P, cadence=C_EXACT, t0_step=C_EXACT / 3,
+            with_kappa=True)
+    g = r["geom"]
+    rng = np.random.default_rng(1)
+    jj = rng.integers(0, 3, 500)
+    ii = rng.integers(0, g.n_t0, 500)
+    d, v, l, k = oracle.linear_cells(g, r["y_grid"], r["w_grid"], durs, r["T"], jj, ii)
+    np.testing.assert_array_equal(d, r["depth"][jj, ii])
+    np.testing.assert_array_equal(l, r["dlogl"][jj, ii])
+    np.testing.assert_array_equal(k, r["kappa"][jj, ii])
+    per = r["periodic"]
+    lr, z, zv = oracle.periodic_at(g, r["depth"], r["depth_var"], r["dlogl"], P, per["i"], per["j"])
+    np.testing.assert_array_equal(lr, per["dlogl"])
+    np.testing.assert_array_equal(z, per["depth"])
