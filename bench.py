@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: light curves searched per second by the CETRA hot path on GB300.
+
+One step = one full search of one light curve: resample -> linear search
+(Sec. 2.2) -> periodic search with in-kernel max (Sec. 2.3) -> FP64 winner
+re-sum. Default workload: a 27-d TESS-like curve at 20-s cadence (116,640
+samples minus a 1-d gap), 20 durations 0.5-12 h, t0 step 20 s, 50,000
+periods 0.5-13.5 d (synthetic, seeded).
+
+  value  device-resident inputs, CUDA-event time of the steps (L2 flushed
+         between steps by a 256 MiB write outside the timed events)
+  e2e    the host-buffer C-ABI calls (cetra_linear_search +
+         cetra_periodic_search) from pinned host memory, copies included
+  --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
+         of each step, extrapolated to curves/s)
+
+Multi-GPU: one process per GPU (torchrun); each rank searches its own curves
+(replicas, no collective on the data path); value = all ranks' curves / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "light curves searched/s on 1 GB300 vs plain form; % FMA/HBM peak; ΔlogL rel err"
+UNIT = "curves/s"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cetra", "reference"], default="cetra")
+    ap.add_argument("--workload", default="tess_20s_27d")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-fold-stride", type=int, default=25,
+                    help="period stride of the oracle's fold sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def fold_cells(info, durations, periods):
+    """Cell reads of the fold: sum over periods k and durations D_j < P_k of
+    sum_e clip(I - o_e, 0, n_phase) (each read is one float2 (A, B))."""
+    I, p, q, c = info["n_t0"], info["p"], info["q"], info["cadence"]
+    total = 0
+    for P in periods:
+        Ps = (P * q) / (c * p)
+        if not (Ps >= 1.0):
+            continue
+        nph = min(I, int(np.ceil(Ps)))
+        e = np.arange(int((I + 0.5) / Ps) + 2, dtype=np.float64)
+        o = np.floor(e * Ps + 0.5).astype(np.int64)
+        cells = int(np.clip(I - o, 0, nph).sum())
+        total += cells * int(np.sum(durations < P))
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"cetra_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(w, stride, durations=None):
+    """The FP64 oracle on this host's cores: the whole linear search plus the
+    fold on every stride-th period, extrapolated to one full curve."""
+    import oracle
+    oracle.build()
+    d = w.durations if durations is None else durations
+    t0 = time.perf_counter()
+    g = oracle.geometry(w.time, w.flux, w.flux_err, d, w.cadence, w.t0_step)
+    y, wg = oracle.resample(w.time, w.flux, w.flux_err, g)
+    T = oracle.template(w.template, 1024)
+    dep, var, lr = oracle.linear(g, y, wg, d, T)
+    t_lin = time.perf_counter() - t0
+    sel = w.periods[::stride]
+    t1 = time.perf_counter()
+    oracle.periodic(g, d, dep, var, lr, sel)
+    t_fold = time.perf_counter() - t1
+    per_curve = t_lin + t_fold * (w.periods.size / sel.size)
+    return {"value": 1.0 / per_curve, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"one {w.name} curve: full linear search ({t_lin:.2f} s) + fold on "
+                       f"{sel.size} of {w.periods.size} periods (every {stride}th, "
+                       f"{t_fold:.2f} s), fold time scaled by {w.periods.size / sel.size:.0f}"),
+            "seconds": t_lin + t_fold}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    w = synth.make_workload(args.workload, seed=1)
+    stride = max(1, args.cpu_fold_stride * 4)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, stride)
+        vals.append(1.0 / last["value"])
+    wall = time.perf_counter() - t0
+    per_curve = sum(vals) / len(vals)
+    value = 1.0 / per_curve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_curve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_points": int(w.time.size),
+                       "n_durations": int(w.durations.size), "n_periods": int(w.periods.size),
+                       "t0_step_s": w.t0_step * 86400, "cadence_s": w.cadence * 86400},
+            "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"],
+                             "value": value, "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import synth
+    import paper_2503_20875_gb300 as cetra
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = synth.make_workload(args.workload, seed=1 + rank)
+    ctx = cetra.Context(local, stream=stream)
+    plan = cetra.Plan(ctx, w.time, w.flux, w.flux_err, w.durations, w.template,
+                      cadence=w.cadence, t0_step=w.t0_step)
+    info = plan.info
+    ds = cetra.DeviceSearch(ctx, plan, w.periods)
+    d_t = torch.as_tensor(w.time, device=dev)
+    d_f = torch.as_tensor(w.flux, device=dev)
+    d_e = torch.as_tensor(w.flux_err, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        ds.run(d_t, d_f, d_e)
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    ctx.profile(True)
+    for k in ("resample", "linear", "fold", "finalize"):
+        ctx.profile_read(k)
+    launches0 = ctx.launches
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)  # evict L2 between steps, outside the timed events
+        starts[s].record(stream)
+        ds.run(d_t, d_f, d_e)
+        ends[s].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    kern = {k: ctx.profile_read(k) for k in ("resample", "linear", "fold", "finalize")}
+    ctx.profile(False)
+    total_s = sum(step_ms) / 1e3
+    t_max = total_s
+    if world > 1:
+        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / t_max
+
+    # ------------------------------------------------------------------ e2e (host buffers)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_t, h_f, h_e = pin(w.time), pin(w.flux), pin(w.flux_err)
+    h_P = pin(w.periods)
+    e2e_times = []
+    best = None
+    for s in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        grid, _, _, _ = cetra.cetra_linear_search(ctx, h_t, h_f, h_e, w.durations, w.template,
+                                                  outputs=False, cadence=w.cadence,
+                                                  t0_step=w.t0_step)
+        per = cetra.cetra_periodic_search(ctx, grid, h_P)
+        best = per["best_k"]
+        grid.close()
+        if s > 0:  # the first call is a warm-up
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
+    e2e_value = world / e2e_t if world == 1 and e2e_times else None
+    if world > 1 and e2e_times:
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_value = world / float(tt.item())
+    h2d = w.time.nbytes + w.flux.nbytes + w.flux_err.nbytes + w.periods.nbytes
+    d2h = 5 * 8 * w.periods.size
+
+    # ------------------------------------------------------------------ roofline (fold)
+    peaks = load_peaks()
+    n_fold, fold_ms = kern["fold"]
+    fold_ms_per = fold_ms / max(n_fold, 1)
+    cells = fold_cells(info, w.durations, w.periods)
+    fold_bytes = 8.0 * cells
+    achieved = fold_bytes / (fold_ms_per * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roofline = {"bound": "hbm", "kernel": "fold_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "algorithmic_bytes_per_launch": fold_bytes, "cell_reads_per_launch": cells,
+                "ms_per_launch": fold_ms_per}
+    n_lin, lin_ms = kern["linear"]
+    lin_ms_per = lin_ms / max(n_lin, 1)
+    lin_fl = 4.0 * sum(info_table_work(plan))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = (peaks or {}).get("sm_max_mhz", 2070.0)
+    fma_peak = sm_count * 128 * 2 * clk * 1e6 / 1e12
+    roofline_linear = {"bound": "alu", "kernel": "linear_kernel",
+                       "achieved": lin_fl / (lin_ms_per * 1e-3) / 1e12, "peak": fma_peak,
+                       "unit": "TFLOP/s", "frac": lin_fl / (lin_ms_per * 1e-3) / 1e12 / fma_peak,
+                       "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 x {clk:.0f} MHz",
+                       "flops_per_launch": lin_fl, "ms_per_launch": lin_ms_per}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_points": int(w.time.size),
+                       "n_grid": int(info["n_grid"]), "n_t0": int(info["n_t0"]),
+                       "n_durations": int(w.durations.size), "n_periods": int(w.periods.size),
+                       "cadence_s": w.cadence * 86400, "t0_step_s": w.t0_step * 86400,
+                       "template_samples": 1024, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h),
+                    "api": "cetra_linear_search + cetra_periodic_search (host buffers, pinned)"},
+            "roofline": roofline, "roofline_linear": roofline_linear,
+            "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kern.items()},
+            "wall_s_timed": wall, "best_period_d": float(w.periods[best]) if best is not None and best >= 0 else None}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_fold_stride)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def info_table_work(plan):
+    """Window points per (duration, class) times t0 points of that class."""
+    from paper_2503_20875_gb300 import _native as N
+    import ctypes
+    info = plan.info
+    I, q, J = info["n_t0"], info["q"], info["n_dur"]
+    # the window length of class r of duration j is what the plan tabulated;
+    # recompute the count from the geometry: points x in [0, 1] per (j, r)
+    c, p = info["cadence"], info["p"]
+    work = []
+    for D in plan.durations:
+        Dt = (D * q) / c
+        for r in range(q):
+            lo = int(np.floor((r * p - 0.5 * Dt) / q)) - 2
+            hi = int(np.ceil((r * p + 0.5 * Dt) / q)) + 2
+            n = np.arange(lo, hi + 1)
+            x = ((n * q - r * p) + 0.5 * Dt) / Dt
+            cnt = int(np.sum((x >= 0) & (x <= 1)))
+            n_t0_r = (I - r + q - 1) // q if r < I else 0
+            work.append(cnt * n_t0_r)
+    return work
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * cetra.h — C ABI of the GB300 (sm_103a) CETRA transit search library.
+ *
+ * The library implements the two GPU stages of CETRA (Smith et al. 2025):
+ * the linear search (Sec. 2.2: a weighted least-squares template fit at every
+ * trial (duration, mid-time) window, Eq. 1 and Eq. 2) and the periodic search
+ * (Sec. 2.3: the linear grid phase-folded over trial periods with a common
+ * depth, Eq. 3 and Eq. 4, reduced in-kernel to the maximum per period).
+ *
+ * Conventions for every entry point
+ *  - Times and durations are in days (FP64). Flux and flux error are FP32;
+ *    flux is normalised to a baseline of 1 unless params.flux_is_offset is
+ *    set (then 0 is baseline and positive values are deficits, Sec. 2).
+ *  - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *    pointers are CUDA device memory on the context's device, owned by the
+ *    caller, and are only touched in stream order on the context's stream.
+ *  - Linear-search arrays are [n_dur][n_t0], row-major, t0 contiguous. The
+ *    t0 grid is t_i = t_ref + (i p - n_pad q) c / q, i = 0 .. n_t0-1, where c
+ *    is the resample cadence, s = c p / q the realised t0 step, and n_pad the
+ *    null padding of Sec. 2.1.1 (see cetra_plan_info).
+ *  - Null results (a window with no data, Sec. 2.2; a period with no valid
+ *    window) are NaN; their indices are -1.
+ *  - Every function returns a cetra_status; on failure cetra_last_error(ctx)
+ *    gives a one-line message. No entry point aborts the process or leaves
+ *    the device in an error state on invalid input.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef CETRA_H
+#define CETRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CETRA_OK = 0,
+    CETRA_EINVAL = 1,    /* invalid argument (sizes, grids, template, no usable points) */
+    CETRA_ENOMEM = 2,    /* host or device allocation failed */
+    CETRA_ECUDA = 3,     /* a CUDA call or kernel launch failed */
+    CETRA_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    CETRA_ECAPACITY = 5  /* an output or workspace buffer is too small */
+} cetra_status;
+
+#define CETRA_FP32 0        /* plain FP32 window and fold sums */
+#define CETRA_FP32_KAHAN 1  /* Kahan-compensated FP32 sums */
+
+typedef struct cetra_ctx cetra_ctx;
+typedef struct cetra_plan cetra_plan;
+typedef struct cetra_linear_grid cetra_linear_grid;
+
+/* Search parameters (Sec. 2.1). Zero / negative values select the paper's defaults. */
+typedef struct {
+    double cadence;        /* resample cadence c (days); <= 0: median input cadence (Sec. 2.1.1) */
+    double t0_step;        /* t0 step s (days); <= 0: 1 % of the shortest duration (Sec. 2.1.3).
+                              Realised as s = c p / q with 1 <= q <= 64 (smallest q within 1e-9
+                              relative, else the closest), so that every index is exact. */
+    int template_samples;  /* L, samples of the resampled template (Sec. 2.1.2); <= 0: 1024 */
+    int flux_is_offset;    /* 0: flux has baseline 1 and y = 1 - f; 1: flux is already y */
+    int precision;         /* CETRA_FP32 or CETRA_FP32_KAHAN */
+} cetra_params;
+
+/* Geometry of a plan (Sec. 2.1.1, Sec. 2.1.3). */
+typedef struct {
+    double t_ref;          /* smallest kept input time (days, absolute) */
+    double cadence;        /* c */
+    double t0_step;        /* s = c p / q */
+    int64_t p, q;          /* s / c = p / q */
+    int64_t n_pad;         /* null points padded at each end: ceil((max D / 2) / c) */
+    int64_t n_grid;        /* resampled grid length N_g */
+    int64_t n_t0;          /* t0 grid length I */
+    int64_t n_kept;        /* input points kept (finite t, f, sigma and sigma > 0) */
+    int32_t n_dur;         /* J */
+    int32_t template_samples;
+    int64_t table_entries; /* window-table entries staged by the linear kernel */
+    size_t grid_bytes;     /* workspace bytes needed without a periodic search */
+} cetra_plan_info;
+
+/* Fill *p with the defaults (median cadence, 1 % t0 step, L = 1024, baseline-1 flux, FP32). */
+void cetra_params_default(cetra_params *p);
+
+/*
+ * Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * the library launches on (NULL: the legacy default stream). The context owns
+ * no large buffers until a host-buffer entry point needs them.
+ * Errors: CETRA_EINVAL (ctx NULL), CETRA_ECUDA (bad device).
+ */
+int cetra_create(cetra_ctx **ctx, int device, void *cuda_stream);
+void cetra_destroy(cetra_ctx *ctx);
+/* Change the stream of a context (e.g. to a torch stream). */
+int cetra_set_stream(cetra_ctx *ctx, void *cuda_stream);
+/* Message of the last failure on this context ("" if none). Owned by ctx. */
+const char *cetra_last_error(const cetra_ctx *ctx);
+/* Number of kernels this context has launched since creation. */
+int64_t cetra_kernel_launches(const cetra_ctx *ctx);
+
+/*
+ * Per-kernel timing (a tracing aid, not in the paper). While enabled, every
+ * launch is bracketed by a pair of CUDA events on the context's stream.
+ * cetra_profile_read synchronises on the recorded events of one kernel
+ * ("resample", "linear", "fold", "finalize", "logl0"), returns the number of
+ * timed launches and their summed device time in milliseconds, and forgets
+ * them. Errors: CETRA_EINVAL (unknown name), CETRA_ECUDA.
+ */
+int cetra_profile_enable(cetra_ctx *ctx, int enable);
+int cetra_profile_read(cetra_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms);
+
+/*
+ * Build a plan: the geometry of the resampled light curve and of the t0 grid
+ * (Sec. 2.1.1, Sec. 2.1.3) from the host times, and the per-duration window
+ * tables of the nearest template sample (Sec. 2.1.2), uploaded to the device.
+ *   time/flux/flux_err  host, n_points each; invalid points (non-finite or
+ *                       sigma <= 0) are ignored.
+ *   durations           host, n_dur > 0 trial durations D_j (days, > 0).
+ *   tmpl                host, tmpl_len >= 1 samples of the transit model
+ *                       from first to last contact; resampled to L samples by
+ *                       linear interpolation and divided by its largest
+ *                       absolute value.
+ * The plan is owned by the caller (cetra_plan_destroy) and may be reused for
+ * any light curve with the same t_ref, cadence and extent.
+ * Errors: CETRA_EINVAL (no usable point, cadence undefined, bad durations or
+ * template), CETRA_ENOMEM, CETRA_ECUDA.
+ */
+int cetra_plan_create(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                      const float *flux, const float *flux_err, int64_t n_points,
+                      const double *durations, int n_dur, const float *tmpl, int tmpl_len,
+                      cetra_plan **plan);
+int cetra_plan_get_info(const cetra_plan *plan, cetra_plan_info *info);
+
+/*
+ * Geometry only (Sec. 2.1.1, Sec. 2.1.3), computed on the host with no device
+ * work: what cetra_plan_create would report in cetra_plan_info, without the
+ * template tables (table_entries = 0). Lets a caller size the [n_dur][n_t0]
+ * outputs of cetra_linear_search before calling it. ctx may be NULL (no
+ * message is then recorded). Errors as cetra_plan_create.
+ */
+int cetra_plan_geometry(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                        const float *flux, const float *flux_err, int64_t n_points,
+                        const double *durations, int n_dur, cetra_plan_info *info);
+void cetra_plan_destroy(cetra_plan *plan);
+
+/* Bytes of device workspace that the device entry points need for n_periods
+ * periods (n_periods = 0: the resample and linear stages only). */
+size_t cetra_workspace_bytes(const cetra_plan *plan, int n_periods);
+
+/*
+ * Device path, stage 1 (Sec. 2.1.1): resample the device light curve onto the
+ * plan's grid inside `d_workspace` (nearest grid point; inverse-variance
+ * combination; empty points null). d_time (FP64), d_flux, d_flux_err (FP32)
+ * are device arrays of n_points. Points that fall outside the plan's grid are
+ * dropped. Stream-ordered; returns after the launches are queued.
+ * Errors: CETRA_EINVAL (NULL pointers, n_points < 0), CETRA_ECUDA.
+ */
+int cetra_resample_device(cetra_ctx *ctx, const cetra_plan *plan, const double *d_time,
+                          const float *d_flux, const float *d_flux_err, int64_t n_points,
+                          void *d_workspace, size_t workspace_bytes);
+
+/*
+ * Device path, stage 2 (Sec. 2.2): the linear search over the resampled grid
+ * in `d_workspace`. Leaves the per-window sufficient statistics
+ * (A = sum m W y, B = sum m^2 W) in the workspace for the periodic stage, and
+ * optionally writes the paper's three outputs (Sec. 2.2): depth = A / B,
+ * depth_var = 1 / B, dlogl = A^2 / (2 B) (which equals Eq. 2 at the
+ * maximum-likelihood depth). d_depth, d_depth_var, d_dlogl: device FP32
+ * [n_dur][n_t0] arrays, each may be NULL. Null windows give NaN.
+ * Errors: CETRA_EINVAL, CETRA_ECAPACITY (workspace too small), CETRA_ECUDA.
+ */
+int cetra_linear_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                        size_t workspace_bytes, float *d_depth, float *d_depth_var,
+                        float *d_dlogl);
+
+/*
+ * Device path, stage 3 (Sec. 2.3): fold the linear grid over the trial
+ * periods d_periods (device FP64, n_periods) with the common-depth model and
+ * reduce in-kernel to the maximum-likelihood window per period. Only D_j < P_k
+ * is evaluated (Sec. 2.3); d_mask (device uint8 [n_periods][n_dur], NULL for
+ * none) can exclude further (D, P) pairs. Epoch cells are the nearest t0
+ * points t_i + e P (Sec. 2.3). Ties go to the smallest duration index, then
+ * the smallest t0 index. Per-period outputs (device arrays of n_periods):
+ * d_dlogl, d_t0 (mid-time, absolute days), d_duration, d_depth (common depth
+ * Z), d_depth_var (var of Z) as FP64, d_i (t0 index, int64), d_j (duration
+ * index, int32). Winners are re-summed in FP64. Any output may be NULL.
+ * Errors: CETRA_EINVAL, CETRA_ECAPACITY, CETRA_ECUDA.
+ */
+int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                          size_t workspace_bytes, const double *d_periods, int n_periods,
+                          const uint8_t *d_mask, double *d_dlogl, double *d_t0,
+                          double *d_duration, double *d_depth, double *d_depth_var,
+                          int64_t *d_i, int32_t *d_j);
+
+/*
+ * Constant-flux log-likelihood (Sec. 2.2, last paragraph): Eq. 1 at zero depth
+ * over the non-null grid points of the resampled curve in d_workspace, written
+ * to *d_logl0 (device FP64). Adding it to any dlogl gives the whole-curve
+ * log-likelihood of that model.
+ */
+int cetra_logl0_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                       size_t workspace_bytes, double *d_logl0);
+
+/*
+ * Host-buffer API: the linear search of Sec. 2.2 on a light curve in host
+ * memory. Copies the inputs in, runs resample + linear search, copies the
+ * three [n_dur][n_t0] FP32 outputs out (each may be NULL), and returns the
+ * device-resident grid in *grid_out (may be NULL) for cetra_periodic_search.
+ * *n_t0: in: capacity of each output row set (elements per duration row);
+ * out: I. If the capacity is too small nothing is written to the outputs and
+ * CETRA_ECAPACITY is returned with *n_t0 = I.
+ * The grid owns its device memory until cetra_grid_free.
+ */
+int cetra_linear_search(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                        const float *flux, const float *flux_err, int64_t n_points,
+                        const double *durations, int n_dur, const float *tmpl, int tmpl_len,
+                        cetra_linear_grid **grid_out, float *depth, float *depth_var,
+                        float *dlogl, int64_t *n_t0);
+
+/*
+ * Host-buffer API: the periodic search of Sec. 2.3 on a grid returned by
+ * cetra_linear_search. periods (host FP64, n_periods), dur_mask (host uint8
+ * [n_periods][n_dur] or NULL). Per-period host outputs (each may be NULL):
+ * dlogl, t0, duration, depth, depth_var (FP64). *best_k (may be NULL): the
+ * period with the largest dlogl (ties: smallest k), -1 if all are null.
+ */
+int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double *periods,
+                          int n_periods, const uint8_t *dur_mask, double *dlogl, double *t0,
+                          double *duration, double *depth, double *depth_var, int64_t *best_k);
+
+/* Release a grid from cetra_linear_search (NULL is allowed). */
+void cetra_grid_free(cetra_linear_grid *grid);
+
+/* Geometry of a grid from cetra_linear_search. */
+int cetra_grid_get_info(const cetra_linear_grid *grid, cetra_plan_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CETRA_H */

@@ -1,0 +1,271 @@
+"""Python face of the CETRA library: thin wrappers over the C ABI (include/cetra.h).
+
+Host-buffer calls take numpy arrays; device calls take torch CUDA tensors
+(PyTorch supplies device memory and streams only). Every stage of the search
+runs in the library's CUDA kernels; nothing here computes any of it.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import check
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+def make_params(cadence=0.0, t0_step=0.0, template_samples=1024, flux_is_offset=False,
+                precision="fp32") -> N.cetra_params:
+    p = N.cetra_params()
+    N.lib.cetra_params_default(ctypes.byref(p))
+    p.cadence = float(cadence or 0.0)
+    p.t0_step = float(t0_step or 0.0)
+    p.template_samples = int(template_samples)
+    p.flux_is_offset = int(bool(flux_is_offset))
+    p.precision = {"fp32": N.CETRA_FP32, "kahan": N.CETRA_FP32_KAHAN}[precision]
+    return p
+
+
+class Context:
+    """A library context on one CUDA device, launching on one stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.handle = ctypes.c_void_p()
+        st = _stream_handle(stream)
+        check(N.lib.cetra_create(ctypes.byref(self.handle), int(device), st), None, "create")
+        self.device = device
+
+    def set_stream(self, stream):
+        check(N.lib.cetra_set_stream(self.handle, _stream_handle(stream)), self.handle)
+
+    @property
+    def launches(self) -> int:
+        return int(N.lib.cetra_kernel_launches(self.handle))
+
+    def profile(self, enable: bool = True):
+        check(N.lib.cetra_profile_enable(self.handle, int(bool(enable))), self.handle)
+
+    def profile_read(self, kernel: str):
+        """(launches, total device ms) of one kernel since the last read."""
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        check(N.lib.cetra_profile_read(self.handle, kernel.encode(), ctypes.byref(n),
+                                       ctypes.byref(ms)), self.handle, "profile_read")
+        return int(n.value), float(ms.value)
+
+    def close(self):
+        if self.handle:
+            N.lib.cetra_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _info_dict(info: N.cetra_plan_info) -> dict:
+    return {f: getattr(info, f) for f, _ in N.cetra_plan_info._fields_}
+
+
+class Plan:
+    """Geometry and window tables of a search (cetra_plan_create)."""
+
+    def __init__(self, ctx: Context, time, flux, flux_err, durations, tmpl, **params):
+        self.ctx = ctx
+        t = _np(time, np.float64)
+        f = _np(flux, np.float32)
+        e = _np(flux_err, np.float32)
+        d = _np(durations, np.float64)
+        tm = _np(tmpl, np.float32)
+        self.durations = d
+        self.params = make_params(**params)
+        self.handle = ctypes.c_void_p()
+        check(N.lib.cetra_plan_create(ctx.handle, ctypes.byref(self.params), _ptr(t), _ptr(f),
+                                      _ptr(e), t.size, _ptr(d), d.size, _ptr(tm), tm.size,
+                                      ctypes.byref(self.handle)), ctx.handle, "plan_create")
+        info = N.cetra_plan_info()
+        check(N.lib.cetra_plan_get_info(self.handle, ctypes.byref(info)), ctx.handle)
+        self.info = _info_dict(info)
+
+    def workspace_bytes(self, n_periods: int = 0) -> int:
+        return int(N.lib.cetra_workspace_bytes(self.handle, int(n_periods)))
+
+    def t0_grid(self) -> np.ndarray:
+        """Mid-times t_i (absolute days) of the t0 grid."""
+        i = np.arange(self.info["n_t0"], dtype=np.int64)
+        ticks = i * self.info["p"] - self.info["n_pad"] * self.info["q"]
+        return self.info["t_ref"] + ticks * self.info["cadence"] / self.info["q"]
+
+    def close(self):
+        if self.handle:
+            N.lib.cetra_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- device path
+
+def cetra_resample_device(ctx: Context, plan: Plan, d_time, d_flux, d_flux_err, workspace):
+    check(N.lib.cetra_resample_device(ctx.handle, plan.handle, _ptr(d_time), _ptr(d_flux),
+                                      _ptr(d_flux_err), int(d_time.numel()), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size()),
+          ctx.handle, "resample_device")
+
+
+def cetra_linear_device(ctx: Context, plan: Plan, workspace, d_depth=None, d_depth_var=None,
+                        d_dlogl=None):
+    check(N.lib.cetra_linear_device(ctx.handle, plan.handle, _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _ptr(d_depth),
+                                    _ptr(d_depth_var), _ptr(d_dlogl)), ctx.handle, "linear_device")
+
+
+def cetra_periodic_device(ctx: Context, plan: Plan, workspace, d_periods, d_mask=None,
+                          out: dict | None = None):
+    out = out or {}
+    check(N.lib.cetra_periodic_device(ctx.handle, plan.handle, _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(),
+                                      _ptr(d_periods), int(d_periods.numel()), _ptr(d_mask),
+                                      _ptr(out.get("dlogl")), _ptr(out.get("t0")),
+                                      _ptr(out.get("duration")), _ptr(out.get("depth")),
+                                      _ptr(out.get("depth_var")), _ptr(out.get("i")),
+                                      _ptr(out.get("j"))),
+          ctx.handle, "periodic_device")
+
+
+def cetra_logl0_device(ctx: Context, plan: Plan, workspace, d_out):
+    check(N.lib.cetra_logl0_device(ctx.handle, plan.handle, _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), _ptr(d_out)),
+          ctx.handle, "logl0_device")
+
+
+class DeviceSearch:
+    """Device buffers (torch) for one plan and one period grid, and the three
+    stages run on them: resample -> linear -> periodic."""
+
+    def __init__(self, ctx: Context, plan: Plan, periods, mask=None, linear_outputs=True):
+        import torch
+        dev = torch.device("cuda", ctx.device)
+        self.ctx, self.plan = ctx, plan
+        K = int(np.size(periods))
+        self.K = K
+        self.workspace = torch.empty(plan.workspace_bytes(K), dtype=torch.uint8, device=dev)
+        self.periods = torch.as_tensor(_np(periods, np.float64), device=dev)
+        self.mask = None if mask is None else torch.as_tensor(_np(mask, np.uint8), device=dev)
+        J, I = plan.info["n_dur"], plan.info["n_t0"]
+        if linear_outputs:
+            self.depth = torch.empty((J, I), dtype=torch.float32, device=dev)
+            self.depth_var = torch.empty_like(self.depth)
+            self.dlogl = torch.empty_like(self.depth)
+        else:
+            self.depth = self.depth_var = self.dlogl = None
+        self.out = {k: torch.empty(K, dtype=torch.float64, device=dev)
+                    for k in ("dlogl", "t0", "duration", "depth", "depth_var")}
+        self.out["i"] = torch.empty(K, dtype=torch.int64, device=dev)
+        self.out["j"] = torch.empty(K, dtype=torch.int32, device=dev)
+        self.logl0 = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def run(self, d_time, d_flux, d_flux_err, periodic=True, logl0=False):
+        cetra_resample_device(self.ctx, self.plan, d_time, d_flux, d_flux_err, self.workspace)
+        cetra_linear_device(self.ctx, self.plan, self.workspace, self.depth, self.depth_var,
+                            self.dlogl)
+        if logl0:
+            cetra_logl0_device(self.ctx, self.plan, self.workspace, self.logl0)
+        if periodic and self.K:
+            cetra_periodic_device(self.ctx, self.plan, self.workspace, self.periods, self.mask,
+                                  self.out)
+        return self
+
+
+# ----------------------------------------------------------------------------- host-buffer path
+
+class LinearGrid:
+    """Device-resident result of cetra_linear_search (owns its device memory)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.handle = ctx, handle
+        info = N.cetra_plan_info()
+        check(N.lib.cetra_grid_get_info(handle, ctypes.byref(info)), ctx.handle)
+        self.info = _info_dict(info)
+
+    def close(self):
+        if self.handle:
+            N.lib.cetra_grid_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cetra_linear_search(ctx: Context, time, flux, flux_err, durations, tmpl, *, outputs=True,
+                        keep_grid=True, **params):
+    """Linear search (Sec. 2.2) on host arrays. Returns (grid, depth, depth_var, dlogl)."""
+    t = _np(time, np.float64)
+    f = _np(flux, np.float32)
+    e = _np(flux_err, np.float32)
+    d = _np(durations, np.float64)
+    tm = _np(tmpl, np.float32)
+    prm = make_params(**params)
+    n_t0 = ctypes.c_int64(0)
+    grid = ctypes.c_void_p()
+    depth = var = lr = None
+    if outputs:
+        info = N.cetra_plan_info()
+        check(N.lib.cetra_plan_geometry(ctx.handle, ctypes.byref(prm), _ptr(t), _ptr(f), _ptr(e),
+                                        t.size, _ptr(d), d.size, ctypes.byref(info)),
+              ctx.handle, "plan_geometry")
+        I = info.n_t0
+        n_t0.value = I
+        depth = np.empty((d.size, I), np.float32)
+        var = np.empty((d.size, I), np.float32)
+        lr = np.empty((d.size, I), np.float32)
+    check(N.lib.cetra_linear_search(ctx.handle, ctypes.byref(prm), _ptr(t), _ptr(f), _ptr(e),
+                                    t.size, _ptr(d), d.size, _ptr(tm), tm.size,
+                                    ctypes.byref(grid) if keep_grid else None, _ptr(depth),
+                                    _ptr(var), _ptr(lr), ctypes.byref(n_t0)),
+          ctx.handle, "linear_search")
+    return (LinearGrid(ctx, grid) if keep_grid else None), depth, var, lr
+
+
+def cetra_periodic_search(ctx: Context, grid: LinearGrid, periods, mask=None) -> dict:
+    """Periodic search (Sec. 2.3) on a grid from cetra_linear_search; host outputs."""
+    P = _np(periods, np.float64)
+    m = None if mask is None else _np(mask, np.uint8)
+    K = P.size
+    out = {k: np.empty(K, np.float64) for k in ("dlogl", "t0", "duration", "depth", "depth_var")}
+    best = ctypes.c_int64(-1)
+    check(N.lib.cetra_periodic_search(ctx.handle, grid.handle, _ptr(P), K, _ptr(m),
+                                      _ptr(out["dlogl"]), _ptr(out["t0"]), _ptr(out["duration"]),
+                                      _ptr(out["depth"]), _ptr(out["depth_var"]),
+                                      ctypes.byref(best)), ctx.handle, "periodic_search")
+    out["best_k"] = best.value
+    return out

@@ -1,0 +1,490 @@
+// C ABI of the CETRA library (declarations and contracts in include/cetra.h).
+// Argument checking, workspace layout, stream-ordered launches and the
+// host-buffer convenience API. No compute happens here: every stage of the
+// search runs in the kernels of kernels.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+int set_error(cetra_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+const char *const kernel_names[KID_COUNT] = {"resample", "linear", "fold", "finalize", "logl0"};
+
+namespace {
+cudaEvent_t pool_event(cetra_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+void prof_mark(cetra_ctx *ctx, kernel_id id, bool begin) {
+    if (!ctx->profiling) return;
+    if (begin) {
+        cudaEvent_t a = pool_event(ctx);
+        if (!a) return;
+        cudaEventRecord(a, ctx->stream);
+        ctx->pending[id].push_back({a, nullptr});
+    } else {
+        if (ctx->pending[id].empty() || ctx->pending[id].back().second) return;
+        cudaEvent_t b = pool_event(ctx);
+        if (!b) return;
+        cudaEventRecord(b, ctx->stream);
+        ctx->pending[id].back().second = b;
+    }
+}
+
+namespace {
+
+int cuda_fail(cetra_ctx *ctx, cudaError_t e, const char *what) {
+    return set_error(ctx, CETRA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct device_guard {
+    int prev = -1;
+    explicit device_guard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~device_guard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// The three device regions of a workspace.
+struct ws_ptrs {
+    float *wy, *w;
+    float2 *ab;
+    unsigned long long *keys;
+    double *logl0;
+};
+
+ws_ptrs carve(void *base, const ws_layout &L) {
+    char *b = static_cast<char *>(base);
+    return ws_ptrs{reinterpret_cast<float *>(b + L.wy), reinterpret_cast<float *>(b + L.w),
+                   reinterpret_cast<float2 *>(b + L.ab),
+                   reinterpret_cast<unsigned long long *>(b + L.keys),
+                   reinterpret_cast<double *>(b + L.logl0)};
+}
+
+void fill_info(const cetra_plan *plan, cetra_plan_info *info) {
+    info->t_ref = plan->t_ref;
+    info->cadence = plan->cadence;
+    info->t0_step = plan->t0_step;
+    info->p = plan->p;
+    info->q = plan->q;
+    info->n_pad = plan->n_pad;
+    info->n_grid = plan->n_grid;
+    info->n_t0 = plan->n_t0;
+    info->n_kept = plan->n_kept;
+    info->n_dur = plan->J;
+    info->template_samples = plan->L;
+    info->table_entries = (int64_t)plan->tables.size();
+    info->grid_bytes = workspace_layout(plan, 0).total;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cetra_params_default(cetra_params *p) {
+    if (!p) return;
+    p->cadence = 0.0;
+    p->t0_step = 0.0;
+    p->template_samples = 1024;
+    p->flux_is_offset = 0;
+    p->precision = CETRA_FP32;
+}
+
+int cetra_create(cetra_ctx **out, int device, void *cuda_stream) {
+    if (!out) return CETRA_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return CETRA_ECUDA;
+    }
+    cetra_ctx *ctx = new (std::nothrow) cetra_ctx;
+    if (!ctx) return CETRA_ENOMEM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    device_guard g(device);
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) == cudaSuccess)
+        ctx->num_sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) == cudaSuccess)
+        ctx->max_smem_optin = (size_t)v;
+    if (ctx->num_sms <= 0) ctx->num_sms = 1;
+    *out = ctx;
+    return CETRA_OK;
+}
+
+void cetra_destroy(cetra_ctx *ctx) {
+    if (!ctx) return;
+    {
+        device_guard g(ctx->device);
+        for (auto &v : ctx->pending)
+            for (auto &pr : v) {
+                if (pr.first) cudaEventDestroy(pr.first);
+                if (pr.second) cudaEventDestroy(pr.second);
+            }
+        for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    }
+    delete ctx;
+}
+
+int cetra_profile_enable(cetra_ctx *ctx, int enable) {
+    if (!ctx) return CETRA_EINVAL;
+    ctx->profiling = enable != 0;
+    return CETRA_OK;
+}
+
+int cetra_profile_read(cetra_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms) {
+    if (!ctx || !kernel) return set_error(ctx, CETRA_EINVAL, "profile_read: NULL argument");
+    int id = -1;
+    for (int k = 0; k < KID_COUNT; ++k)
+        if (std::strcmp(kernel, kernel_names[k]) == 0) id = k;
+    if (id < 0) return set_error(ctx, CETRA_EINVAL, std::string("profile_read: unknown kernel ") + kernel);
+    device_guard g(ctx->device);
+    double sum = 0.0;
+    int64_t n = 0;
+    for (auto &pr : ctx->pending[id]) {
+        if (pr.second) {
+            if (cudaEventSynchronize(pr.second) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "profile_read");
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+                sum += ms;
+                ++n;
+            }
+            ctx->event_pool.push_back(pr.second);
+        }
+        ctx->event_pool.push_back(pr.first);
+    }
+    ctx->pending[id].clear();
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = sum;
+    return CETRA_OK;
+}
+
+int cetra_set_stream(cetra_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return CETRA_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return CETRA_OK;
+}
+
+const char *cetra_last_error(const cetra_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int64_t cetra_kernel_launches(const cetra_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int cetra_plan_create(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                      const float *flux, const float *flux_err, int64_t n_points,
+                      const double *durations, int n_dur, const float *tmpl, int tmpl_len,
+                      cetra_plan **plan_out) {
+    if (!ctx || !plan_out) return set_error(ctx, CETRA_EINVAL, "plan: NULL ctx or plan");
+    *plan_out = nullptr;
+    cetra_params def;
+    cetra_params_default(&def);
+    if (!params) params = &def;
+    if (params->precision != CETRA_FP32 && params->precision != CETRA_FP32_KAHAN)
+        return set_error(ctx, CETRA_EINVAL, "plan: unknown precision");
+    device_guard g(ctx->device);
+    cetra_plan *plan = new (std::nothrow) cetra_plan;
+    if (!plan) return set_error(ctx, CETRA_ENOMEM, "plan: host allocation");
+    plan->device = ctx->device;
+    int rc = plan_build(ctx, params, time, flux, flux_err, n_points, durations, n_dur, tmpl,
+                        tmpl_len, plan, true);
+    if (rc == CETRA_OK && (int64_t)plan->J * plan->q > 65535)
+        rc = set_error(ctx, CETRA_EINVAL, "plan: n_dur * q exceeds 65535");
+    if (rc == CETRA_OK) rc = plan_upload(ctx, plan);
+    if (rc != CETRA_OK) {
+        plan_free_device(plan);
+        delete plan;
+        return rc;
+    }
+    *plan_out = plan;
+    return CETRA_OK;
+}
+
+int cetra_plan_geometry(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                        const float *flux, const float *flux_err, int64_t n_points,
+                        const double *durations, int n_dur, cetra_plan_info *info) {
+    if (!info) return set_error(ctx, CETRA_EINVAL, "geometry: NULL info");
+    cetra_params def;
+    cetra_params_default(&def);
+    if (!params) params = &def;
+    cetra_plan plan;
+    int rc = plan_build(ctx, params, time, flux, flux_err, n_points, durations, n_dur, nullptr, 0,
+                        &plan, false);
+    if (rc != CETRA_OK) return rc;
+    fill_info(&plan, info);
+    return CETRA_OK;
+}
+
+int cetra_plan_get_info(const cetra_plan *plan, cetra_plan_info *info) {
+    if (!plan || !info) return CETRA_EINVAL;
+    fill_info(plan, info);
+    return CETRA_OK;
+}
+
+void cetra_plan_destroy(cetra_plan *plan) {
+    if (!plan) return;
+    device_guard g(plan->device);
+    plan_free_device(plan);
+    delete plan;
+}
+
+size_t cetra_workspace_bytes(const cetra_plan *plan, int n_periods) {
+    return plan ? workspace_layout(plan, n_periods).total : 0;
+}
+
+int cetra_resample_device(cetra_ctx *ctx, const cetra_plan *plan, const double *d_time,
+                          const float *d_flux, const float *d_flux_err, int64_t n_points,
+                          void *d_workspace, size_t workspace_bytes) {
+    if (!ctx || !plan || !d_workspace) return set_error(ctx, CETRA_EINVAL, "resample: NULL argument");
+    if (n_points < 0) return set_error(ctx, CETRA_EINVAL, "resample: n_points < 0");
+    if (n_points > 0 && (!d_time || !d_flux || !d_flux_err))
+        return set_error(ctx, CETRA_EINVAL, "resample: NULL input array");
+    ws_layout L = workspace_layout(plan, 0);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "resample: workspace too small");
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = cudaMemsetAsync(w.wy, 0, L.ab - L.wy, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "resample memset");
+    e = launch_resample(ctx, plan, d_time, d_flux, d_flux_err, n_points, w.wy, w.w);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "resample launch");
+    return CETRA_OK;
+}
+
+int cetra_linear_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                        size_t workspace_bytes, float *d_depth, float *d_depth_var,
+                        float *d_dlogl) {
+    if (!ctx || !plan || !d_workspace) return set_error(ctx, CETRA_EINVAL, "linear: NULL argument");
+    ws_layout L = workspace_layout(plan, 0);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "linear: workspace too small");
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = launch_linear(ctx, plan, w.wy, w.w, w.ab, d_depth, d_depth_var, d_dlogl);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "linear launch");
+    return CETRA_OK;
+}
+
+int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                          size_t workspace_bytes, const double *d_periods, int n_periods,
+                          const uint8_t *d_mask, double *d_dlogl, double *d_t0,
+                          double *d_duration, double *d_depth, double *d_depth_var,
+                          int64_t *d_i, int32_t *d_j) {
+    if (!ctx || !plan || !d_workspace) return set_error(ctx, CETRA_EINVAL, "periodic: NULL argument");
+    if (n_periods < 0) return set_error(ctx, CETRA_EINVAL, "periodic: n_periods < 0");
+    if (n_periods == 0) return CETRA_OK;
+    if (!d_periods) return set_error(ctx, CETRA_EINVAL, "periodic: NULL periods");
+    ws_layout L = workspace_layout(plan, n_periods);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "periodic: workspace too small");
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = launch_fold(ctx, plan, w.ab, d_periods, n_periods, d_mask, w.keys);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fold launch");
+    e = launch_finalize(ctx, plan, w.ab, d_periods, n_periods, w.keys, d_dlogl, d_t0, d_duration,
+                        d_depth, d_depth_var, d_i, d_j);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "finalize launch");
+    return CETRA_OK;
+}
+
+int cetra_logl0_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                       size_t workspace_bytes, double *d_logl0) {
+    if (!ctx || !plan || !d_workspace || !d_logl0)
+        return set_error(ctx, CETRA_EINVAL, "logl0: NULL argument");
+    ws_layout L = workspace_layout(plan, 0);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "logl0: workspace too small");
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = launch_logl0(ctx, plan, w.wy, w.w, d_logl0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "logl0 launch");
+    return CETRA_OK;
+}
+
+// ------------------------------------------------------------------------------ host-buffer API
+
+int cetra_linear_search(cetra_ctx *ctx, const cetra_params *params, const double *time,
+                        const float *flux, const float *flux_err, int64_t n_points,
+                        const double *durations, int n_dur, const float *tmpl, int tmpl_len,
+                        cetra_linear_grid **grid_out, float *depth, float *depth_var,
+                        float *dlogl, int64_t *n_t0) {
+    if (!ctx) return CETRA_EINVAL;
+    if (grid_out) *grid_out = nullptr;
+    if ((depth || depth_var || dlogl) && !n_t0)
+        return set_error(ctx, CETRA_EINVAL, "linear_search: n_t0 capacity required with outputs");
+    cetra_plan *plan = nullptr;
+    int rc = cetra_plan_create(ctx, params, time, flux, flux_err, n_points, durations, n_dur, tmpl,
+                               tmpl_len, &plan);
+    if (rc) return rc;
+    const int64_t I = plan->n_t0;
+    if ((depth || depth_var || dlogl) && *n_t0 < I) {
+        *n_t0 = I;
+        cetra_plan_destroy(plan);
+        return set_error(ctx, CETRA_ECAPACITY, "linear_search: output capacity below n_t0");
+    }
+    if (n_t0) *n_t0 = I;
+    device_guard g(ctx->device);
+    cetra_linear_grid *grid = new (std::nothrow) cetra_linear_grid;
+    if (!grid) {
+        cetra_plan_destroy(plan);
+        return set_error(ctx, CETRA_ENOMEM, "linear_search: host allocation");
+    }
+    grid->ctx = ctx;
+    grid->plan = plan;
+    grid->work_bytes = workspace_layout(plan, 0).total;
+    auto fail = [&](int code) {
+        cetra_grid_free(grid);
+        return code;
+    };
+    cudaError_t e = cudaMalloc(&grid->d_work, grid->work_bytes);
+    if (e != cudaSuccess) {
+        grid->d_work = nullptr;
+        return fail(set_error(ctx, CETRA_ENOMEM, "linear_search: workspace allocation"));
+    }
+    // inputs
+    const size_t nb_t = (size_t)n_points * sizeof(double), nb_f = (size_t)n_points * sizeof(float);
+    void *d_in = nullptr;
+    e = cudaMalloc(&d_in, nb_t + 2 * nb_f + 64);
+    if (e != cudaSuccess) return fail(set_error(ctx, CETRA_ENOMEM, "linear_search: input allocation"));
+    double *d_t = static_cast<double *>(d_in);
+    float *d_f = reinterpret_cast<float *>(static_cast<char *>(d_in) + nb_t);
+    float *d_e = d_f + n_points;
+    cudaMemcpyAsync(d_t, time, nb_t, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(d_f, flux, nb_f, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(d_e, flux_err, nb_f, cudaMemcpyHostToDevice, ctx->stream);
+    rc = cetra_resample_device(ctx, plan, d_t, d_f, d_e, n_points, grid->d_work, grid->work_bytes);
+    float *d_out = nullptr;
+    const size_t cells = (size_t)plan->J * (size_t)I;
+    int nout = (depth ? 1 : 0) + (depth_var ? 1 : 0) + (dlogl ? 1 : 0);
+    if (rc == CETRA_OK && nout) {
+        e = cudaMalloc((void **)&d_out, cells * sizeof(float) * nout);
+        if (e != cudaSuccess) rc = set_error(ctx, CETRA_ENOMEM, "linear_search: output allocation");
+    }
+    if (rc == CETRA_OK) {
+        float *o = d_out;
+        float *dd = depth ? o : nullptr;
+        if (depth) o += cells;
+        float *dv = depth_var ? o : nullptr;
+        if (depth_var) o += cells;
+        float *dl = dlogl ? o : nullptr;
+        rc = cetra_linear_device(ctx, plan, grid->d_work, grid->work_bytes, dd, dv, dl);
+        if (rc == CETRA_OK) {
+            if (depth) cudaMemcpyAsync(depth, dd, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (depth_var) cudaMemcpyAsync(depth_var, dv, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (dlogl) cudaMemcpyAsync(dlogl, dl, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        }
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (rc != CETRA_OK) return fail(rc);
+    if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "linear_search"));
+    if (grid_out)
+        *grid_out = grid;
+    else
+        cetra_grid_free(grid);
+    return CETRA_OK;
+}
+
+int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double *periods,
+                          int n_periods, const uint8_t *dur_mask, double *dlogl, double *t0,
+                          double *duration, double *depth, double *depth_var, int64_t *best_k) {
+    if (!ctx || !grid || !grid->plan) return set_error(ctx, CETRA_EINVAL, "periodic_search: NULL grid");
+    if (n_periods < 0 || (n_periods > 0 && !periods))
+        return set_error(ctx, CETRA_EINVAL, "periodic_search: bad periods");
+    for (int k = 0; k < n_periods; ++k)
+        if (!(periods[k] > 0.0) || !std::isfinite(periods[k]))
+            return set_error(ctx, CETRA_EINVAL, "periodic_search: periods must be finite and > 0");
+    if (best_k) *best_k = -1;
+    if (n_periods == 0) return CETRA_OK;
+    cetra_plan *plan = grid->plan;
+    device_guard g(ctx->device);
+    // the grid workspace is sized without keys; periodic needs a larger one
+    ws_layout L = workspace_layout(plan, n_periods);
+    if (grid->work_bytes < L.total) {
+        void *bigger = nullptr;
+        cudaError_t e = cudaMalloc(&bigger, L.total);
+        if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "periodic_search: workspace allocation");
+        e = cudaMemcpyAsync(bigger, grid->d_work, grid->work_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(bigger);
+            return cuda_fail(ctx, e, "periodic_search: workspace copy");
+        }
+        cudaFree(grid->d_work);
+        grid->d_work = bigger;
+        grid->work_bytes = L.total;
+    }
+    const size_t K = (size_t)n_periods, J = (size_t)plan->J;
+    const size_t bytes = K * sizeof(double) * 6 + K * J + 256;
+    char *d_buf = nullptr;
+    cudaError_t e = cudaMalloc((void **)&d_buf, bytes);
+    if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "periodic_search: buffer allocation");
+    double *d_P = reinterpret_cast<double *>(d_buf);
+    double *d_out = d_P + K;  // 5 K doubles
+    uint8_t *d_mask = dur_mask ? reinterpret_cast<uint8_t *>(d_out + 5 * K) : nullptr;
+    cudaMemcpyAsync(d_P, periods, K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (dur_mask) cudaMemcpyAsync(d_mask, dur_mask, K * J, cudaMemcpyHostToDevice, ctx->stream);
+    int rc = cetra_periodic_device(ctx, plan, grid->d_work, grid->work_bytes, d_P, n_periods,
+                                   d_mask, d_out, d_out + K, d_out + 2 * K, d_out + 3 * K,
+                                   d_out + 4 * K, nullptr, nullptr);
+    double *h_lr = dlogl;
+    std::vector<double> tmp;
+    if (!h_lr && best_k) {
+        tmp.resize(K);
+        h_lr = tmp.data();
+    }
+    if (rc == CETRA_OK) {
+        if (h_lr) cudaMemcpyAsync(h_lr, d_out, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (t0) cudaMemcpyAsync(t0, d_out + K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (duration) cudaMemcpyAsync(duration, d_out + 2 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (depth) cudaMemcpyAsync(depth, d_out + 3 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (depth_var) cudaMemcpyAsync(depth_var, d_out + 4 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d_buf);
+    if (rc != CETRA_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "periodic_search");
+    if (best_k && h_lr) {
+        int64_t bk = -1;
+        double bv = -INFINITY;
+        for (size_t k = 0; k < K; ++k)
+            if (!std::isnan(h_lr[k]) && h_lr[k] > bv) {
+                bv = h_lr[k];
+                bk = (int64_t)k;
+            }
+        *best_k = bk;
+    }
+    return CETRA_OK;
+}
+
+void cetra_grid_free(cetra_linear_grid *grid) {
+    if (!grid) return;
+    if (grid->plan) {
+        device_guard g(grid->plan->device);
+        cudaFree(grid->d_work);
+    }
+    cetra_plan_destroy(grid->plan);
+    delete grid;
+}
+
+int cetra_grid_get_info(const cetra_linear_grid *grid, cetra_plan_info *info) {
+    if (!grid || !grid->plan || !info) return CETRA_EINVAL;
+    fill_info(grid->plan, info);
+    return CETRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the host planner (plan.cpp), the C ABI
+// (capi.cpp) and the kernels (kernels.cu). Not installed, not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cetra.h"
+
+// Kernels the library launches, for per-kernel event timing.
+enum kernel_id { KID_RESAMPLE = 0, KID_LINEAR, KID_FOLD, KID_FINALIZE, KID_LOGL0, KID_COUNT };
+extern const char *const kernel_names[KID_COUNT];
+
+struct cetra_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int64_t launches = 0;
+    int num_sms = 0;
+    size_t max_smem_optin = 0;
+    // event timing (cetra_profile_enable): one start/stop pair per launch
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KID_COUNT];
+    std::vector<cudaEvent_t> event_pool;
+};
+
+// Record a start (begin = true) or stop event around a launch when profiling.
+void prof_mark(cetra_ctx *ctx, kernel_id id, bool begin);
+
+// Geometry and window tables (Sec. 2.1). Built on the host in FP64, the tables
+// uploaded once. Window tables: for every duration j and t0 phase class
+// r = i mod q, the grid points of the window of t0 index i = r + q u are
+// n = a[j][r] + p u + k, k = 0 .. len[j][r]-1, with template samples tab[k].
+struct cetra_plan {
+    int device = 0;
+    double t_ref = 0, cadence = 0, t0_step = 0, tau_max = 0;
+    int64_t p = 1, q = 1, n_pad = 0, n_grid = 0, n_t0 = 0, n_kept = 0;
+    int J = 0, L = 0;
+    int flux_is_offset = 0, precision = 0;
+    std::vector<double> durations;
+    std::vector<double> T;             // resampled template (FP64)
+    std::vector<int32_t> win_a;        // [J*q] first grid point (class base, may be < 0)
+    std::vector<int32_t> win_len;      // [J*q] window length
+    std::vector<int32_t> win_padlen;   // [J*q] length padded to the kernel's multiple
+    std::vector<int64_t> win_off;      // [J*q] offset into the table array
+    std::vector<float2> tables;        // (m, m^2) per window point
+    int32_t max_padlen = 0;
+    // linear kernel launch shape, chosen from p and the table lengths
+    int lin_threads = 128, lin_kc = 0;
+    size_t lin_smem = 0;
+    // device copies (owned)
+    double *d_durations = nullptr;
+    int32_t *d_win_a = nullptr, *d_win_len = nullptr, *d_win_padlen = nullptr;
+    int64_t *d_win_off = nullptr;
+    float2 *d_tables = nullptr;
+};
+
+struct cetra_linear_grid {
+    cetra_ctx *ctx = nullptr;
+    cetra_plan *plan = nullptr;
+    void *d_work = nullptr;
+    size_t work_bytes = 0;
+};
+
+// Register block of the linear kernel: outputs per thread. Odd, so that the
+// stride-RB shared-memory reads of a warp fall in distinct banks.
+constexpr int LIN_RB = 9;
+constexpr int FOLD_THREADS = 256;
+constexpr int FOLD_EMAX = 8192;  // epochs held in shared memory by the fold kernel
+
+// Workspace layout (byte offsets, 256-aligned).
+struct ws_layout {
+    size_t wy, w, ab, keys, logl0, total;
+};
+ws_layout workspace_layout(const cetra_plan *plan, int n_periods);
+
+// Host planner (plan.cpp)
+int plan_build(cetra_ctx *ctx, const cetra_params *params, const double *time, const float *flux,
+               const float *flux_err, int64_t n_points, const double *durations, int n_dur,
+               const float *tmpl, int tmpl_len, cetra_plan *plan, bool with_tables);
+int plan_upload(cetra_ctx *ctx, cetra_plan *plan);
+void plan_free_device(cetra_plan *plan);
+
+// Kernel launchers (kernels.cu). Return cudaSuccess or the launch error.
+cudaError_t launch_resample(cetra_ctx *ctx, const cetra_plan *plan, const double *time,
+                            const float *flux, const float *err, int64_t n, float *wy, float *w);
+cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
+                          float2 *ab, float *depth, float *var, float *dlogl);
+cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
+                        const double *periods, int K, const uint8_t *mask,
+                        unsigned long long *keys);
+cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
+                            const double *periods, int K, const unsigned long long *keys,
+                            double *dlogl, double *t0, double *dur, double *depth, double *var,
+                            int64_t *oi, int32_t *oj);
+cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
+                         double *out);
+cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx);
+
+int set_error(cetra_ctx *ctx, int code, const std::string &msg);
