@@ -69,8 +69,10 @@ struct cetra_linear_grid {
 // Register block of the linear kernel: outputs per thread. Odd, so that the
 // stride-RB shared-memory reads of a warp fall in distinct banks.
 constexpr int LIN_RB = 9;
+constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear kernel
 constexpr int FOLD_THREADS = 256;
-constexpr int FOLD_EMAX = 8192;  // epochs held in shared memory by the fold kernel
+constexpr int FOLD_G = 8;          // periods folded together by one block
+constexpr int FOLD_TABLE = 12288;  // epoch-offset entries (48 KiB) of the grouped fold
 
 // Workspace layout (byte offsets, 256-aligned).
 struct ws_layout {

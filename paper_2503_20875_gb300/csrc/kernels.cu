@@ -3,8 +3,8 @@
 //   resample_kernel   Sec. 2.1.1  nearest-grid-point scatter of (W y, W), W = 1/sigma^2
 //   linear_kernel     Sec. 2.2    per (duration, t0): A = sum m W y, B = sum m^2 W over the
 //                                 window; depth = A/B, var = 1/B, dlogl = A^2/(2B)
-//   fold_kernel       Sec. 2.3    per period: sum A and B over the epoch cells of every
-//                                 (duration, phase), LR = SA^2/(2 SB), in-kernel max/argmax
+//   fold_group_kernel Sec. 2.3    per group of periods: sum A and B over the epoch cells of
+//                                 every (duration, phase), LR = SA^2/(2 SB), in-kernel max/argmax
 //   finalize_kernel   Sec. 2.3    FP64 re-sum of each period's winner: Z, var_Z, LR, t0
 //   logl0_kernel      Sec. 2.2    constant-flux log-likelihood (Eq. 1 at zero depth)
 //
@@ -109,9 +109,12 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
     float2 *st = smem;           // [kc_max] template chunk (m, m^2)
     float2 *sd = smem + kc_max;  // [p*UT + kc_max] grid span (W y, W)
 
-    float2 acc[RB];
+    // Blocked summation: `acc` collects at most LIN_SUB * RB terms before it is
+    // folded into `tot`, so the FP32 rounding error grows with the block length
+    // plus the number of blocks instead of with the window length.
+    float2 acc[RB], tot[RB];
 #pragma unroll
-    for (int rr = 0; rr < RB; ++rr) acc[rr] = make_float2(0.f, 0.f);
+    for (int rr = 0; rr < RB; ++rr) acc[rr] = tot[rr] = make_float2(0.f, 0.f);
 
     for (int kc0 = 0; kc0 < padlen; kc0 += kc_max) {
         const int kcl = min(kc_max, padlen - kc0);
@@ -133,18 +136,28 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
             float2 buf[RB];
 #pragma unroll
             for (int rr = 0; rr < RB; ++rr) buf[rr] = V[p * rr];
-            for (int kb = 0; kb < nk1; kb += RB) {
+            for (int kb0 = 0; kb0 < nk1; kb0 += LIN_SUB * RB) {
+                const int kb_end = min(nk1, kb0 + LIN_SUB * RB);
+                for (int kb = kb0; kb < kb_end; kb += RB) {
 #pragma unroll
-                for (int s = 0; s < RB; ++s) {
-                    const int k1 = kb + s;
-                    const float2 mm = M[p * k1];
+                    for (int s = 0; s < RB; ++s) {
+                        const int k1 = kb + s;
+                        const float2 mm = M[p * k1];
 #pragma unroll
-                    for (int rr = 0; rr < RB; ++rr) fma2(acc[rr], mm, buf[(s + rr) % RB]);
-                    buf[s] = V[p * (k1 + RB)];
+                        for (int rr = 0; rr < RB; ++rr) fma2(acc[rr], mm, buf[(s + rr) % RB]);
+                        buf[s] = V[p * (k1 + RB)];
+                    }
+                }
+#pragma unroll
+                for (int rr = 0; rr < RB; ++rr) {
+                    add2(tot[rr], acc[rr]);
+                    acc[rr] = make_float2(0.f, 0.f);
                 }
             }
         }
     }
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) acc[rr] = tot[rr];
 
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
@@ -191,83 +204,173 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long v
 }
 
 // --------------------------------------------------------------------------------------------
-// Sec. 2.3 periodic search. One block per period (grid-stride). The epoch offsets
-// o_e are computed once per period in FP64 into shared memory; each thread then
-// folds phases i (strided by blockDim) for every duration with D_j < P_k:
-// SA = sum_e A[j][i + o_e], SB = sum_e B[j][i + o_e] (coalesced 8-byte loads along i),
-// LR = SA^2 / (2 SB). The block reduces to one key per period.
-__global__ void __launch_bounds__(FOLD_THREADS)
-fold_kernel(const float2 *__restrict__ ab, int64_t I, int J, const double *__restrict__ durations,
-            const double *__restrict__ periods, int K, const uint8_t *__restrict__ mask, double c,
-            int64_t p, int64_t q, unsigned long long *__restrict__ keys) {
-    __shared__ int32_t off[FOLD_EMAX];
+// Sec. 2.3 periodic search, FOLD_G periods per block. Neighbouring trial periods
+// gather nearly the same epoch cells (their offsets differ by a few cells), so a
+// thread folds its phase i for all FOLD_G periods together: the first period's
+// loads bring the cache lines into L1 and the others hit them. The epoch offsets
+// of the group live in shared memory as [e][g]. A group whose offsets do not fit
+// is folded one period at a time (table of that period only), and a period
+// whose own table does not fit computes its offsets on the fly in FP64.
+#ifndef FOLD_MIN_BLOCKS
+#define FOLD_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(FOLD_THREADS, FOLD_MIN_BLOCKS)
+fold_group_kernel(const float2 *__restrict__ ab, int64_t I, int J,
+                  const double *__restrict__ durations, const double *__restrict__ periods, int K,
+                  const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q,
+                  unsigned long long *__restrict__ keys) {
+    extern __shared__ int32_t off[];  // FOLD_TABLE entries
     __shared__ unsigned long long red[FOLD_THREADS / 32];
+    __shared__ unsigned long long s_best[FOLD_G][FOLD_THREADS];  // per-thread best key per period
+    __shared__ double s_P[FOLD_G], s_Ps[FOLD_G];
+    __shared__ int64_t s_nph[FOLD_G];
+    __shared__ int s_E[FOLD_G];
     const int t = threadIdx.x;
-    for (int k = blockIdx.x; k < K; k += gridDim.x) {
-        const double P = periods[k];
-        const double Ps = period_steps(P, c, p, q);
-        // a period shorter than one t0 step (or not finite) has no distinct phase: null
-        if (!(Ps >= 1.0) || !isfinite(Ps)) {
-            if (t == 0) keys[k] = 0ull;
-            continue;
+    const int ngroups = (K + FOLD_G - 1) / FOLD_G;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int k0 = grp * FOLD_G;
+        __syncthreads();  // the previous group is done with the shared tables
+        if (t < FOLD_G) {
+            const int k = k0 + t;
+            double P = 0.0, Ps = 0.0;
+            int64_t nph = 0;
+            int E = 0;
+            if (k < K) {
+                P = periods[k];
+                Ps = period_steps(P, c, p, q);
+                // a period shorter than one t0 step (or not finite) has no distinct phase: null
+                if (Ps >= 1.0 && isfinite(Ps)) {
+                    const double cph = ceil(Ps);
+                    nph = cph < (double)I ? (int64_t)cph : I;
+                    const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
+                    E = eb < 2147483647.0 ? (int)eb : 2147483647;
+                }
+            }
+            s_P[t] = P;
+            s_Ps[t] = Ps;
+            s_nph[t] = nph;
+            s_E[t] = E;
         }
-        const double cph = ceil(Ps);
-        const int64_t nph = cph < (double)I ? (int64_t)cph : I;
-        // epochs with o_e < I number at most floor((I + 1/2) / Ps) + 1
-        const double ebound = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
-        const bool in_smem = ebound <= (double)FOLD_EMAX;
-        int E = 0;
         __syncthreads();
-        if (in_smem) {
-            E = (int)ebound;
-            for (int e = t; e < E; e += blockDim.x) {
-                const int64_t o = epoch_offset(e, Ps);
-                off[e] = o < I ? (int32_t)o : INT32_MAX;
+        int Emax = 0;
+        int64_t nphmax = 0;
+#pragma unroll
+        for (int g = 0; g < FOLD_G; ++g) {
+            Emax = max(Emax, s_E[g]);
+            nphmax = max(nphmax, s_nph[g]);
+        }
+        const bool grouped = (int64_t)Emax * FOLD_G <= FOLD_TABLE;
+        if (grouped) {
+            for (int idx = t; idx < Emax * FOLD_G; idx += blockDim.x) {
+                const int e = idx / FOLD_G, g = idx % FOLD_G;
+                int32_t o = INT32_MAX;
+                if (e < s_E[g]) {
+                    const int64_t v = epoch_offset(e, s_Ps[g]);
+                    if (v < I) o = (int32_t)v;
+                }
+                off[idx] = o;
             }
         }
         __syncthreads();
-        unsigned long long best = 0ull;
-        for (int j = 0; j < J; ++j) {
-            if (!(durations[j] < P)) continue;
-            if (mask && !mask[(int64_t)k * J + j]) continue;
-            const float2 *row = ab + (int64_t)j * I;
-            for (int64_t i = t; i < nph; i += blockDim.x) {
-                float2 s = make_float2(0.f, 0.f);
-                if (in_smem) {
-                    int e = 0;
-                    for (; e + 4 <= E; e += 4) {
-                        const int o3 = off[e + 3];
-                        if (i + (int64_t)o3 >= I) break;
-                        const float2 v0 = row[i + off[e]];
-                        const float2 v1 = row[i + off[e + 1]];
-                        const float2 v2 = row[i + off[e + 2]];
-                        const float2 v3 = row[i + o3];
-                        add2(s, v0);
-                        add2(s, v1);
-                        add2(s, v2);
-                        add2(s, v3);
+
+#pragma unroll
+        for (int g = 0; g < FOLD_G; ++g) s_best[g][t] = 0ull;
+
+        if (grouped) {
+            for (int j = 0; j < J; ++j) {
+                const double D = durations[j];
+                unsigned use = 0u;
+#pragma unroll
+                for (int g = 0; g < FOLD_G; ++g) {
+                    const int k = k0 + g;
+                    if (s_E[g] > 0 && D < s_P[g] && (!mask || mask[(int64_t)k * J + j]))
+                        use |= 1u << g;
+                }
+                if (!use) continue;
+                const float2 *row = ab + (int64_t)j * I;
+                for (int64_t i = t; i < nphmax; i += blockDim.x) {
+                    unsigned act = 0u;
+#pragma unroll
+                    for (int g = 0; g < FOLD_G; ++g)
+                        if (((use >> g) & 1u) && i < s_nph[g]) act |= 1u << g;
+                    float2 acc[FOLD_G];
+#pragma unroll
+                    for (int g = 0; g < FOLD_G; ++g) acc[g] = make_float2(0.f, 0.f);
+                    for (int e = 0; e < Emax && act; ++e) {
+                        const int4 oa = *reinterpret_cast<const int4 *>(&off[e * FOLD_G]);
+                        const int4 ob = *reinterpret_cast<const int4 *>(&off[e * FOLD_G + 4]);
+                        const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+                        unsigned live = 0u;
+#pragma unroll
+                        for (int g = 0; g < FOLD_G; ++g) {
+                            if (((act >> g) & 1u) && i + (int64_t)o[g] < I) {
+                                add2(acc[g], row[i + o[g]]);
+                                live |= 1u << g;
+                            }
+                        }
+                        act = live;  // offsets grow with e: a period past the end stays past it
                     }
-                    for (; e < E; ++e) {
-                        const int o = off[e];
-                        if (i + (int64_t)o >= I) break;
-                        add2(s, row[i + o]);
-                    }
-                } else {
-                    for (int64_t e = 0;; ++e) {
-                        const int64_t cell = i + epoch_offset(e, Ps);
-                        if (cell >= I) break;
-                        add2(s, row[cell]);
+#pragma unroll
+                    for (int g = 0; g < FOLD_G; ++g) {
+                        if (acc[g].y > 0.0f && ((use >> g) & 1u) && i < s_nph[g]) {
+                            const float lr = 0.5f * (acc[g].x * (acc[g].x / acc[g].y));
+                            const unsigned long long key =
+                                make_key(lr, (uint32_t)((int64_t)j * I + i));
+                            if (key > s_best[g][t]) s_best[g][t] = key;
+                        }
                     }
                 }
-                if (s.y > 0.0f) {
-                    const float lr = 0.5f * (s.x * (s.x / s.y));
-                    const unsigned long long key = make_key(lr, (uint32_t)((int64_t)j * I + i));
-                    best = key > best ? key : best;
+            }
+        } else {
+            // one period at a time: its own offsets in the table when they fit
+#pragma unroll
+            for (int g = 0; g < FOLD_G; ++g) {
+                const int E = s_E[g];
+                const double Ps = s_Ps[g];
+                const bool tab = E <= FOLD_TABLE;
+                __syncthreads();
+                if (tab)
+                    for (int e = t; e < E; e += blockDim.x) {
+                        const int64_t v = epoch_offset(e, Ps);
+                        off[e] = v < I ? (int32_t)v : INT32_MAX;
+                    }
+                __syncthreads();
+                if (E == 0) continue;
+                const int k = k0 + g;
+                for (int j = 0; j < J; ++j) {
+                    if (!(durations[j] < s_P[g])) continue;
+                    if (mask && !mask[(int64_t)k * J + j]) continue;
+                    const float2 *row = ab + (int64_t)j * I;
+                    for (int64_t i = t; i < s_nph[g]; i += blockDim.x) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        if (tab) {
+                            for (int e = 0; e < E; ++e) {
+                                const int o = off[e];
+                                if (i + (int64_t)o >= I) break;
+                                add2(acc, row[i + o]);
+                            }
+                        } else {
+                            for (int64_t e = 0;; ++e) {
+                                const int64_t cell = i + epoch_offset(e, Ps);
+                                if (cell >= I) break;
+                                add2(acc, row[cell]);
+                            }
+                        }
+                        if (acc.y > 0.0f) {
+                            const float lr = 0.5f * (acc.x * (acc.x / acc.y));
+                            const unsigned long long key =
+                                make_key(lr, (uint32_t)((int64_t)j * I + i));
+                            if (key > s_best[g][t]) s_best[g][t] = key;
+                        }
+                    }
                 }
             }
         }
-        best = block_max_key(best, red);
-        if (t == 0) keys[k] = best;
+#pragma unroll
+        for (int g = 0; g < FOLD_G; ++g) {
+            const unsigned long long v = block_max_key(s_best[g][t], red);
+            if (t == 0 && k0 + g < K) keys[k0 + g] = v;
+        }
     }
 }
 
@@ -405,9 +508,10 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
                         unsigned long long *keys) {
     if (K <= 0) return cudaSuccess;
     prof_mark(ctx, KID_FOLD, true);
-    fold_kernel<<<K, FOLD_THREADS, 0, ctx->stream>>>(ab, plan->n_t0, plan->J, plan->d_durations,
-                                                     periods, K, mask, plan->cadence, plan->p,
-                                                     plan->q, keys);
+    const int ngroups = (K + FOLD_G - 1) / FOLD_G;
+    fold_group_kernel<<<ngroups, FOLD_THREADS, FOLD_TABLE * sizeof(int32_t), ctx->stream>>>(
+        ab, plan->n_t0, plan->J, plan->d_durations, periods, K, mask, plan->cadence, plan->p,
+        plan->q, keys);
     prof_mark(ctx, KID_FOLD, false);
     ctx->launches++;
     return cudaGetLastError();
