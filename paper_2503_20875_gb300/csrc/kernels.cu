@@ -482,8 +482,13 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
     plan->lin_smem = bytes(threads, kc);
     size_t limit = ctx->max_smem_optin ? ctx->max_smem_optin : 227 * 1024;
     if (plan->lin_smem > limit) return cudaErrorInvalidConfiguration;
-    return cudaFuncSetAttribute(linear_kernel<LIN_RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)plan->lin_smem);
+    cudaError_t e = cudaFuncSetAttribute(linear_kernel<LIN_RB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plan->lin_smem);
+    if (e != cudaSuccess) return e;
+    // the grouped fold's offset table (dynamic) plus its per-thread keys (static) exceed 48 KiB
+    return cudaFuncSetAttribute(fold_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(FOLD_TABLE * sizeof(int32_t)));
 }
 
 cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
