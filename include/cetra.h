@@ -191,6 +191,14 @@ int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_worksp
                           int64_t *d_i, int32_t *d_j);
 
 /*
+ * Status word of a workspace after cetra_periodic_device: 0, or CETRA_ETIMEOUT
+ * if a bounded device-side wait of the fold gave up (its outputs are then NaN).
+ * Synchronises the context's stream.
+ */
+int cetra_workspace_status(cetra_ctx *ctx, const cetra_plan *plan, const void *d_workspace,
+                           size_t workspace_bytes, int *status);
+
+/*
  * Constant-flux log-likelihood (Sec. 2.2, last paragraph): Eq. 1 at zero depth
  * over the non-null grid points of the resampled curve in d_workspace, written
  * to *d_logl0 (device FP64). Adding it to any dlogl gives the whole-curve

@@ -68,6 +68,7 @@ struct ws_ptrs {
     float2 *ab;
     unsigned long long *keys;
     double *logl0;
+    int *status;
 };
 
 ws_ptrs carve(void *base, const ws_layout &L) {
@@ -75,7 +76,7 @@ ws_ptrs carve(void *base, const ws_layout &L) {
     return ws_ptrs{reinterpret_cast<float *>(b + L.wy), reinterpret_cast<float *>(b + L.w),
                    reinterpret_cast<float2 *>(b + L.ab),
                    reinterpret_cast<unsigned long long *>(b + L.keys),
-                   reinterpret_cast<double *>(b + L.logl0)};
+                   reinterpret_cast<double *>(b + L.logl0), reinterpret_cast<int *>(b + L.status)};
 }
 
 void fill_info(const cetra_plan *plan, cetra_plan_info *info) {
@@ -275,7 +276,13 @@ int cetra_linear_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspac
     if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "linear: workspace too small");
     device_guard g(ctx->device);
     ws_ptrs w = carve(d_workspace, L);
-    cudaError_t e = launch_linear(ctx, plan, w.wy, w.w, w.ab, d_depth, d_depth_var, d_dlogl);
+    // the zero cells after each grid row, read by the fold's bulk copies
+    const size_t pitch = (size_t)plan->ab_ld * sizeof(float2);
+    cudaError_t e = cudaMemset2DAsync(w.ab + plan->n_t0, pitch, 0,
+                                      (size_t)(plan->ab_ld - plan->n_t0) * sizeof(float2),
+                                      (size_t)plan->J, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "linear padding memset");
+    e = launch_linear(ctx, plan, w.wy, w.w, w.ab, d_depth, d_depth_var, d_dlogl);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "linear launch");
     return CETRA_OK;
 }
@@ -293,11 +300,29 @@ int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_worksp
     if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "periodic: workspace too small");
     device_guard g(ctx->device);
     ws_ptrs w = carve(d_workspace, L);
-    cudaError_t e = launch_fold(ctx, plan, w.ab, d_periods, n_periods, d_mask, w.keys);
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "periodic status memset");
+    e = launch_fold(ctx, plan, w.ab, d_periods, n_periods, d_mask, w.keys, w.status);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fold launch");
-    e = launch_finalize(ctx, plan, w.ab, d_periods, n_periods, w.keys, d_dlogl, d_t0, d_duration,
-                        d_depth, d_depth_var, d_i, d_j);
+    e = launch_finalize(ctx, plan, w.ab, d_periods, n_periods, w.keys, w.status, d_dlogl, d_t0,
+                        d_duration, d_depth, d_depth_var, d_i, d_j);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "finalize launch");
+    return CETRA_OK;
+}
+
+int cetra_workspace_status(cetra_ctx *ctx, const cetra_plan *plan, const void *d_workspace,
+                           size_t workspace_bytes, int *status) {
+    if (!ctx || !plan || !d_workspace || !status)
+        return set_error(ctx, CETRA_EINVAL, "workspace_status: NULL argument");
+    ws_layout L = workspace_layout(plan, 0);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "workspace_status: workspace too small");
+    device_guard g(ctx->device);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(d_workspace) + L.status,
+                                    sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace_status");
+    *status = v;
     return CETRA_OK;
 }
 
@@ -458,6 +483,10 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
     cudaFree(d_buf);
     if (rc != CETRA_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "periodic_search");
+    int st = 0;
+    rc = cetra_workspace_status(ctx, plan, grid->d_work, grid->work_bytes, &st);
+    if (rc != CETRA_OK) return rc;
+    if (st != 0) return set_error(ctx, CETRA_ETIMEOUT, "periodic_search: a device wait timed out");
     if (best_k && h_lr) {
         int64_t bk = -1;
         double bv = -INFINITY;

@@ -49,6 +49,7 @@ struct cetra_plan {
     std::vector<int64_t> win_off;      // [J*q] offset into the table array
     std::vector<float2> tables;        // (m, m^2) per window point
     int32_t max_padlen = 0;
+    int64_t ab_ld = 0;  // row stride (cells) of the (A, B) grid: n_t0 + zero padding, even
     // linear kernel launch shape, chosen from p and the table lengths
     int lin_threads = 128, lin_kc = 0;
     size_t lin_smem = 0;
@@ -71,12 +72,31 @@ struct cetra_linear_grid {
 constexpr int LIN_RB = 9;
 constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear kernel
 constexpr int FOLD_THREADS = 256;
-constexpr int FOLD_G = 8;          // periods folded together by one block
-constexpr int FOLD_TABLE = 12288;  // epoch-offset entries (48 KiB) of the grouped fold
+
+// Fold kernel shape (compile-time; see fold_tma_kernel).
+#ifndef FT_R
+#define FT_R 4            // phases per thread
+#endif
+#ifndef FT_STRIP
+#define FT_STRIP 2560     // cells per staged strip
+#endif
+#ifndef FT_NSTAGE
+#define FT_NSTAGE 3       // strips in flight per block
+#endif
+#ifndef FT_MIN_BLOCKS
+#define FT_MIN_BLOCKS 2
+#endif
+constexpr int FT_THREADS = 256;
+constexpr int FT_T = FT_THREADS * FT_R;  // phases per tile
+constexpr int FT_G = 8;                  // periods per block
+constexpr int FT_TABLE = 8192;           // epoch-offset table entries (32 KiB)
+constexpr uint32_t FT_SPIN_LIMIT = 1u << 21;  // polls of a bulk-copy barrier before giving up
+constexpr int FOLD_PAD = FT_STRIP + 16;  // zero cells after each grid row
+size_t fold_smem_bytes();
 
 // Workspace layout (byte offsets, 256-aligned).
 struct ws_layout {
-    size_t wy, w, ab, keys, logl0, total;
+    size_t wy, w, ab, keys, logl0, status, total;
 };
 ws_layout workspace_layout(const cetra_plan *plan, int n_periods);
 
@@ -94,10 +114,10 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
                           float2 *ab, float *depth, float *var, float *dlogl);
 cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
                         const double *periods, int K, const uint8_t *mask,
-                        unsigned long long *keys);
+                        unsigned long long *keys, int *status);
 cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
                             const double *periods, int K, const unsigned long long *keys,
-                            double *dlogl, double *t0, double *dur, double *depth, double *var,
+                            const int *status, double *dlogl, double *t0, double *dur, double *depth, double *var,
                             int64_t *oi, int32_t *oj);
 cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
                          double *out);

@@ -3,7 +3,7 @@
 //   resample_kernel   Sec. 2.1.1  nearest-grid-point scatter of (W y, W), W = 1/sigma^2
 //   linear_kernel     Sec. 2.2    per (duration, t0): A = sum m W y, B = sum m^2 W over the
 //                                 window; depth = A/B, var = 1/B, dlogl = A^2/(2B)
-//   fold_group_kernel Sec. 2.3    per group of periods: sum A and B over the epoch cells of
+//   fold_tma_kernel   Sec. 2.3    per group of periods: sum A and B over the epoch cells of
 //                                 every (duration, phase), LR = SA^2/(2 SB), in-kernel max/argmax
 //   finalize_kernel   Sec. 2.3    FP64 re-sum of each period's winner: Z, var_Z, LR, t0
 //   logl0_kernel      Sec. 2.2    constant-flux log-likelihood (Eq. 1 at zero depth)
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(128)
 linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
               const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
-              int q, int64_t I, int kc_max, float2 *__restrict__ ab, float *__restrict__ depth,
+              int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
+              float *__restrict__ depth,
               float *__restrict__ var, float *__restrict__ dlogl) {
     extern __shared__ float2 smem[];
     const int nthr = blockDim.x;
@@ -166,7 +167,7 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
         const int64_t i = r + (int64_t)q * u;
         const int64_t idx = (int64_t)j * I + i;
         const float A = acc[rr].x, B = acc[rr].y;
-        ab[idx] = acc[rr];
+        ab[(int64_t)j * ld + i] = acc[rr];
         const bool ok = B > 0.0f;
         if (depth) depth[idx] = ok ? A / B : __int_as_float(0x7fc00000);
         if (var) var[idx] = ok ? 1.0f / B : __int_as_float(0x7fc00000);
@@ -204,33 +205,99 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long v
 }
 
 // --------------------------------------------------------------------------------------------
-// Sec. 2.3 periodic search, FOLD_G periods per block. Neighbouring trial periods
-// gather nearly the same epoch cells (their offsets differ by a few cells), so a
-// thread folds its phase i for all FOLD_G periods together: the first period's
-// loads bring the cache lines into L1 and the others hit them. The epoch offsets
-// of the group live in shared memory as [e][g]. A group whose offsets do not fit
-// is folded one period at a time (table of that period only), and a period
-// whose own table does not fit computes its offsets on the fly in FP64.
-#ifndef FOLD_MIN_BLOCKS
-#define FOLD_MIN_BLOCKS 1
-#endif
-__global__ void __launch_bounds__(FOLD_THREADS, FOLD_MIN_BLOCKS)
-fold_group_kernel(const float2 *__restrict__ ab, int64_t I, int J,
-                  const double *__restrict__ durations, const double *__restrict__ periods, int K,
-                  const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q,
-                  unsigned long long *__restrict__ keys) {
-    extern __shared__ int32_t off[];  // FOLD_TABLE entries
-    __shared__ unsigned long long red[FOLD_THREADS / 32];
-    __shared__ unsigned long long s_best[FOLD_G][FOLD_THREADS];  // per-thread best key per period
-    __shared__ double s_P[FOLD_G], s_Ps[FOLD_G];
-    __shared__ int64_t s_nph[FOLD_G];
-    __shared__ int s_E[FOLD_G];
+// Shared-memory barriers and 1-D bulk copies (TMA) used by the fold.
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy; src and dst 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_done(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within FT_SPIN_LIMIT polls
+// (non-blocking polls with a short back-off: well under a second in total).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < FT_SPIN_LIMIT; ++it) {
+        if (mbar_done(bar, parity)) return true;
+        if (it >= 32) __nanosleep(64);
+    }
+    return false;
+}
+
+// --------------------------------------------------------------------------------------------
+// Sec. 2.3 periodic search. One block folds a group of FT_G consecutive trial periods
+// over every duration. Neighbouring periods gather nearly the same epoch cells, so
+// for a tile of FT_T phases and an epoch e the block copies the union of the cells
+// the group needs, [i0 + min_g o_e(g), i0 + max_g o_e(g) + FT_T), into shared memory
+// with one bulk copy (FT_NSTAGE-deep ring, one mbarrier per stage) and every period
+// reads its cells from there: the grid is read from L2 about once per group instead
+// of once per period. Thread t owns phases i0 + t + r * FT_THREADS (r < FT_R) of
+// every period of the group, summing (A, B) over epochs in ascending order.
+// Grid rows carry FOLD_PAD zero cells after the last t0, so a strip never needs
+// clipping: cells past the end contribute (0, 0).
+// Groups whose offsets spread too far apart for one strip are split (8 -> 4 -> 2 -> 1);
+// a period with more epochs than the offset table holds is folded straight from
+// global memory with its offsets computed in FP64 on the fly.
+constexpr int32_t FT_SENT = INT32_MAX;  // epoch past the end of the t0 grid
+
+__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
+fold_tma_kernel(const float2 *__restrict__ ab, int64_t I, int64_t ld, int J,
+                const double *__restrict__ durations, const double *__restrict__ periods, int K,
+                const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q,
+                unsigned long long *__restrict__ keys, int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *strips = reinterpret_cast<float2 *>(smem_raw);                      // [NSTAGE][STRIP]
+    int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);  // FT_TABLE
+    __shared__ __align__(8) uint64_t bar[FT_NSTAGE];
+    __shared__ unsigned long long red[FT_THREADS / 32];
+    __shared__ unsigned long long s_best[FT_G][FT_THREADS];
+    __shared__ double s_P[FT_G], s_Ps[FT_G];
+    __shared__ int64_t s_nph[FT_G];
+    __shared__ int s_E[FT_G];
+    __shared__ int s_bad;
+
     const int t = threadIdx.x;
-    const int ngroups = (K + FOLD_G - 1) / FOLD_G;
+    if (t == 0) {
+        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&bar[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t issued = 0, consumed = 0;  // bulk copies issued (thread 0) / waited (all threads)
+
+    const int ngroups = (K + FT_G - 1) / FT_G;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int k0 = grp * FOLD_G;
+        const int k0 = grp * FT_G;
         __syncthreads();  // the previous group is done with the shared tables
-        if (t < FOLD_G) {
+        if (t < FT_G) {
             const int k = k0 + t;
             double P = 0.0, Ps = 0.0;
             int64_t nph = 0;
@@ -251,123 +318,168 @@ fold_group_kernel(const float2 *__restrict__ ab, int64_t I, int J,
             s_nph[t] = nph;
             s_E[t] = E;
         }
+        for (int g = 0; g < FT_G; ++g) s_best[g][t] = 0ull;
         __syncthreads();
-        int Emax = 0;
-        int64_t nphmax = 0;
-#pragma unroll
-        for (int g = 0; g < FOLD_G; ++g) {
-            Emax = max(Emax, s_E[g]);
-            nphmax = max(nphmax, s_nph[g]);
-        }
-        const bool grouped = (int64_t)Emax * FOLD_G <= FOLD_TABLE;
-        if (grouped) {
-            for (int idx = t; idx < Emax * FOLD_G; idx += blockDim.x) {
-                const int e = idx / FOLD_G, g = idx % FOLD_G;
-                int32_t o = INT32_MAX;
-                if (e < s_E[g]) {
-                    const int64_t v = epoch_offset(e, s_Ps[g]);
-                    if (v < I) o = (int32_t)v;
+
+        for (int g0 = 0; g0 < FT_G;) {
+            // ---- choose the sub-group [g0, g0 + Gs) and build its offset table
+            int Gs = FT_G;
+            while (g0 % Gs) Gs >>= 1;
+            int Es = 0;
+            bool table_ok = false;
+            for (;;) {
+                Es = 0;
+                for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, s_E[g]);
+                // table: offsets [e][Gs], then min offset [e], then strip length [e]
+                if ((int64_t)Es * (Gs + 2) > FT_TABLE) {
+                    if (Gs > 1) {
+                        Gs >>= 1;
+                        continue;
+                    }
+                    break;  // a single period with too many epochs: no table
                 }
-                off[idx] = o;
+                __syncthreads();
+                if (t == 0) s_bad = 0;
+                for (int idx = t; idx < Es * Gs; idx += blockDim.x) {
+                    const int e = idx / Gs, g = g0 + idx % Gs;
+                    int32_t o = FT_SENT;
+                    if (e < s_E[g]) {
+                        const int64_t v = epoch_offset(e, s_Ps[g]);
+                        if (v < I) o = (int32_t)v;
+                    }
+                    tab[idx] = o;
+                }
+                __syncthreads();
+                int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es;
+                bool bad = false;
+                for (int e = t; e < Es; e += blockDim.x) {
+                    int32_t mn = FT_SENT, mx = -1;
+                    for (int gg = 0; gg < Gs; ++gg) {
+                        const int32_t o = tab[e * Gs + gg];
+                        if (o != FT_SENT) {
+                            mn = min(mn, o);
+                            mx = max(mx, o);
+                        }
+                    }
+                    tmin[e] = mn;
+                    tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
+                    if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
+                }
+                if (bad) s_bad = 1;
+                __syncthreads();
+                if (s_bad && Gs > 1) {
+                    Gs >>= 1;
+                    continue;
+                }
+                table_ok = !s_bad;
+                break;
             }
-        }
-        __syncthreads();
+            const int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es;
+            int64_t nph_sub = 0;
+            for (int g = g0; g < g0 + Gs; ++g) nph_sub = max(nph_sub, s_nph[g]);
 
-#pragma unroll
-        for (int g = 0; g < FOLD_G; ++g) s_best[g][t] = 0ull;
-
-        if (grouped) {
-            for (int j = 0; j < J; ++j) {
+            for (int j = 0; j < J && nph_sub > 0; ++j) {
                 const double D = durations[j];
                 unsigned use = 0u;
-#pragma unroll
-                for (int g = 0; g < FOLD_G; ++g) {
-                    const int k = k0 + g;
-                    if (s_E[g] > 0 && D < s_P[g] && (!mask || mask[(int64_t)k * J + j]))
-                        use |= 1u << g;
+                for (int gg = 0; gg < Gs; ++gg) {
+                    const int g = g0 + gg;
+                    if (s_E[g] > 0 && D < s_P[g] && (!mask || mask[(int64_t)(k0 + g) * J + j]))
+                        use |= 1u << gg;
                 }
                 if (!use) continue;
-                const float2 *row = ab + (int64_t)j * I;
-                for (int64_t i = t; i < nphmax; i += blockDim.x) {
-                    unsigned act = 0u;
-#pragma unroll
-                    for (int g = 0; g < FOLD_G; ++g)
-                        if (((use >> g) & 1u) && i < s_nph[g]) act |= 1u << g;
-                    float2 acc[FOLD_G];
-#pragma unroll
-                    for (int g = 0; g < FOLD_G; ++g) acc[g] = make_float2(0.f, 0.f);
-                    for (int e = 0; e < Emax && act; ++e) {
-                        const int4 oa = *reinterpret_cast<const int4 *>(&off[e * FOLD_G]);
-                        const int4 ob = *reinterpret_cast<const int4 *>(&off[e * FOLD_G + 4]);
-                        const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
-                        unsigned live = 0u;
-#pragma unroll
-                        for (int g = 0; g < FOLD_G; ++g) {
-                            if (((act >> g) & 1u) && i + (int64_t)o[g] < I) {
-                                add2(acc[g], row[i + o[g]]);
-                                live |= 1u << g;
-                            }
-                        }
-                        act = live;  // offsets grow with e: a period past the end stays past it
-                    }
-#pragma unroll
-                    for (int g = 0; g < FOLD_G; ++g) {
-                        if (acc[g].y > 0.0f && ((use >> g) & 1u) && i < s_nph[g]) {
-                            const float lr = 0.5f * (acc[g].x * (acc[g].x / acc[g].y));
-                            const unsigned long long key =
-                                make_key(lr, (uint32_t)((int64_t)j * I + i));
-                            if (key > s_best[g][t]) s_best[g][t] = key;
-                        }
-                    }
-                }
-            }
-        } else {
-            // one period at a time: its own offsets in the table when they fit
-#pragma unroll
-            for (int g = 0; g < FOLD_G; ++g) {
-                const int E = s_E[g];
-                const double Ps = s_Ps[g];
-                const bool tab = E <= FOLD_TABLE;
-                __syncthreads();
-                if (tab)
-                    for (int e = t; e < E; e += blockDim.x) {
-                        const int64_t v = epoch_offset(e, Ps);
-                        off[e] = v < I ? (int32_t)v : INT32_MAX;
-                    }
-                __syncthreads();
-                if (E == 0) continue;
-                const int k = k0 + g;
-                for (int j = 0; j < J; ++j) {
-                    if (!(durations[j] < s_P[g])) continue;
-                    if (mask && !mask[(int64_t)k * J + j]) continue;
-                    const float2 *row = ab + (int64_t)j * I;
-                    for (int64_t i = t; i < s_nph[g]; i += blockDim.x) {
+                const float2 *row = ab + (int64_t)j * ld;
+
+                if (!table_ok) {
+                    // one period, offsets on the fly (FP64), straight from global memory
+                    const double Ps = s_Ps[g0];
+                    for (int64_t i = t; i < s_nph[g0]; i += blockDim.x) {
                         float2 acc = make_float2(0.f, 0.f);
-                        if (tab) {
-                            for (int e = 0; e < E; ++e) {
-                                const int o = off[e];
-                                if (i + (int64_t)o >= I) break;
-                                add2(acc, row[i + o]);
-                            }
-                        } else {
-                            for (int64_t e = 0;; ++e) {
-                                const int64_t cell = i + epoch_offset(e, Ps);
-                                if (cell >= I) break;
-                                add2(acc, row[cell]);
-                            }
+                        for (int64_t e = 0;; ++e) {
+                            const int64_t cell = i + epoch_offset(e, Ps);
+                            if (cell >= I) break;
+                            add2(acc, row[cell]);
                         }
                         if (acc.y > 0.0f) {
                             const float lr = 0.5f * (acc.x * (acc.x / acc.y));
                             const unsigned long long key =
                                 make_key(lr, (uint32_t)((int64_t)j * I + i));
-                            if (key > s_best[g][t]) s_best[g][t] = key;
+                            if (key > s_best[g0][t]) s_best[g0][t] = key;
+                        }
+                    }
+                    continue;
+                }
+
+                for (int64_t i0 = 0; i0 < nph_sub; i0 += FT_T) {
+                    float2 acc[FT_G][FT_R];
+#pragma unroll
+                    for (int gg = 0; gg < FT_G; ++gg)
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+                    // epochs of this tile: a prefix (min offsets grow with e)
+                    auto live = [&](int e) { return e < Es && i0 + (int64_t)tmin[e] < I; };
+                    auto issue = [&](int e) {
+                        const int st = issued % FT_NSTAGE;
+                        const int64_t a = (i0 + (int64_t)tmin[e]) & ~(int64_t)1;
+                        int64_t len = i0 + (int64_t)tmin[e] + tlen[e] + FT_T - a;
+                        len = (len + 1) & ~(int64_t)1;
+                        const uint32_t bytes = (uint32_t)(len * (int64_t)sizeof(float2));
+                        fence_proxy_async();
+                        mbar_expect_tx(&bar[st], bytes);
+                        bulk_load(strips + st * FT_STRIP, row + a, bytes, &bar[st]);
+                        ++issued;
+                    };
+                    if (t == 0)
+                        for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
+                    for (int e = 0; live(e); ++e) {
+                        if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
+                        const int st = consumed % FT_NSTAGE;
+                        const bool ok = mbar_wait(&bar[st], (consumed / FT_NSTAGE) & 1u);
+                        ++consumed;
+                        const float2 *S = strips + st * FT_STRIP;
+                        const int64_t a = (i0 + (int64_t)tmin[e]) & ~(int64_t)1;
+#pragma unroll
+                        for (int gg = 0; gg < FT_G; ++gg) {
+                            if (gg >= Gs || !((use >> gg) & 1u)) continue;
+                            const int32_t o = tab[e * Gs + gg];
+                            if (o == FT_SENT) continue;
+                            const float2 *src = S + (i0 + o - a) + t;
+#pragma unroll
+                            for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], src[r * FT_THREADS]);
+                        }
+                        if (__syncthreads_or(!ok)) {
+                            // a copy did not land in time: record it, drain, stop
+                            if (t == 0) {
+                                atomicExch(status, CETRA_ETIMEOUT);
+                                while (consumed < issued) {
+                                    mbar_wait(&bar[consumed % FT_NSTAGE],
+                                              (consumed / FT_NSTAGE) & 1u);
+                                    ++consumed;
+                                }
+                            }
+                            return;
+                        }
+                    }
+#pragma unroll
+                    for (int gg = 0; gg < FT_G; ++gg) {
+                        if (gg >= Gs || !((use >> gg) & 1u)) continue;
+                        const int g = g0 + gg;
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) {
+                            const int64_t i = i0 + t + r * FT_THREADS;
+                            const float2 v = acc[gg][r];
+                            if (i < s_nph[g] && v.y > 0.0f) {
+                                const float lr = 0.5f * (v.x * (v.x / v.y));
+                                const unsigned long long key =
+                                    make_key(lr, (uint32_t)((int64_t)j * I + i));
+                                if (key > s_best[g][t]) s_best[g][t] = key;
+                            }
                         }
                     }
                 }
             }
+            g0 += Gs;
         }
-#pragma unroll
-        for (int g = 0; g < FOLD_G; ++g) {
+        for (int g = 0; g < FT_G; ++g) {
             const unsigned long long v = block_max_key(s_best[g][t], red);
             if (t == 0 && k0 + g < K) keys[k0 + g] = v;
         }
@@ -376,17 +488,18 @@ fold_group_kernel(const float2 *__restrict__ ab, int64_t I, int J,
 
 // --------------------------------------------------------------------------------------------
 // Sec. 2.3: the per-period winner, re-summed in FP64 from the FP32 grid.
-__global__ void finalize_kernel(const float2 *__restrict__ ab, int64_t I,
+__global__ void finalize_kernel(const float2 *__restrict__ ab, int64_t I, int64_t ld,
                                 const double *__restrict__ durations,
                                 const double *__restrict__ periods, int K,
-                                const unsigned long long *__restrict__ keys, double t_ref, double c,
+                                const unsigned long long *__restrict__ keys,
+                                const int *__restrict__ status, double t_ref, double c,
                                 int64_t p, int64_t q, int64_t n_pad, double *dlogl, double *t0,
                                 double *dur, double *depth, double *var, int64_t *oi, int32_t *oj) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const unsigned long long key = keys[k];
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    if (key == 0ull) {
+    if (key == 0ull || *status != 0) {  // null period, or the fold gave up
         if (dlogl) dlogl[k] = nan;
         if (t0) t0[k] = nan;
         if (dur) dur[k] = nan;
@@ -399,7 +512,7 @@ __global__ void finalize_kernel(const float2 *__restrict__ ab, int64_t I,
     const uint32_t flat = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull);
     const int64_t j = (int64_t)flat / I, i = (int64_t)flat % I;
     const double Ps = period_steps(periods[k], c, p, q);
-    const float2 *row = ab + j * I;
+    const float2 *row = ab + j * ld;
     double SA = 0.0, SB = 0.0;
     for (int64_t e = 0;; ++e) {
         const int64_t cell = i + epoch_offset(e, Ps);
@@ -448,6 +561,10 @@ __global__ void logl0_kernel(const float *__restrict__ wy, const float *__restri
 
 }  // namespace
 
+size_t fold_smem_bytes() {
+    return (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2) + (size_t)FT_TABLE * sizeof(int32_t);
+}
+
 // ============================================================================================
 // launchers
 
@@ -486,9 +603,9 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan->lin_smem);
     if (e != cudaSuccess) return e;
-    // the grouped fold's offset table (dynamic) plus its per-thread keys (static) exceed 48 KiB
-    return cudaFuncSetAttribute(fold_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(FOLD_TABLE * sizeof(int32_t)));
+    // the fold's strip ring and offset table (dynamic) exceed the default 48 KiB
+    return cudaFuncSetAttribute(fold_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fold_smem_bytes());
 }
 
 cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
@@ -502,7 +619,7 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
     prof_mark(ctx, KID_LINEAR, true);
     linear_kernel<LIN_RB><<<grid, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
         wy, w, plan->n_grid, plan->d_tables, plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
-        (int)plan->p, (int)q, I, plan->lin_kc, ab, depth, var, dlogl);
+        (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, ab, depth, var, dlogl);
     prof_mark(ctx, KID_LINEAR, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -510,13 +627,13 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
 
 cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
                         const double *periods, int K, const uint8_t *mask,
-                        unsigned long long *keys) {
+                        unsigned long long *keys, int *status) {
     if (K <= 0) return cudaSuccess;
+    const int ngroups = (K + FT_G - 1) / FT_G;
     prof_mark(ctx, KID_FOLD, true);
-    const int ngroups = (K + FOLD_G - 1) / FOLD_G;
-    fold_group_kernel<<<ngroups, FOLD_THREADS, FOLD_TABLE * sizeof(int32_t), ctx->stream>>>(
-        ab, plan->n_t0, plan->J, plan->d_durations, periods, K, mask, plan->cadence, plan->p,
-        plan->q, keys);
+    fold_tma_kernel<<<ngroups, FT_THREADS, fold_smem_bytes(), ctx->stream>>>(
+        ab, plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
+        plan->cadence, plan->p, plan->q, keys, status);
     prof_mark(ctx, KID_FOLD, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -524,13 +641,14 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
 
 cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
                             const double *periods, int K, const unsigned long long *keys,
-                            double *dlogl, double *t0, double *dur, double *depth, double *var,
+                            const int *status, double *dlogl, double *t0, double *dur, double *depth, double *var,
                             int64_t *oi, int32_t *oj) {
     if (K <= 0) return cudaSuccess;
     const int threads = 128;
     prof_mark(ctx, KID_FINALIZE, true);
     finalize_kernel<<<(K + threads - 1) / threads, threads, 0, ctx->stream>>>(
-        ab, plan->n_t0, plan->d_durations, periods, K, keys, plan->t_ref, plan->cadence, plan->p,
+        ab, plan->n_t0, plan->ab_ld, plan->d_durations, periods, K, keys, status, plan->t_ref,
+        plan->cadence, plan->p,
         plan->q, plan->n_pad, dlogl, t0, dur, depth, var, oi, oj);
     prof_mark(ctx, KID_FINALIZE, false);
     ctx->launches++;

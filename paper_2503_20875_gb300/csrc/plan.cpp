@@ -141,6 +141,7 @@ int plan_build(cetra_ctx *ctx, const cetra_params *params, const double *time, c
     plan->durations.assign(durations, durations + n_dur);
     if (plan->n_grid > (int64_t)INT32_MAX / 2 || plan->n_t0 * (int64_t)n_dur > (int64_t)UINT32_MAX)
         return set_error(ctx, CETRA_EINVAL, "plan: grid too large (n_dur * n_t0 must fit 32 bits)");
+    plan->ab_ld = ((plan->n_t0 + FOLD_PAD) + 1) & ~(int64_t)1;
     if (!with_tables) return CETRA_OK;
 
     // --- template (Sec. 2.1.2): linear interpolation to L samples over
@@ -260,9 +261,11 @@ ws_layout workspace_layout(const cetra_plan *plan, int n_periods) {
     L.w = off;
     off = up(off + ng * sizeof(float));
     L.ab = off;
-    off = up(off + (size_t)plan->J * (size_t)plan->n_t0 * sizeof(float2));
+    off = up(off + (size_t)plan->J * (size_t)plan->ab_ld * sizeof(float2));
     L.logl0 = off;
     off = up(off + sizeof(double));
+    L.status = off;
+    off = up(off + sizeof(int));
     L.keys = off;
     off = up(off + (size_t)std::max(n_periods, 0) * sizeof(unsigned long long));
     L.total = off;
