@@ -269,29 +269,197 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // global memory with its offsets computed in FP64 on the fly.
 constexpr int32_t FT_SENT = INT32_MAX;  // epoch past the end of the t0 grid
 
+// Shared state of the fold block.
+struct fold_smem {
+    uint64_t bar[FT_NSTAGE];
+    unsigned long long red[FT_THREADS / 32];
+    unsigned long long best[FT_G][FT_THREADS];
+    double P[FT_G], Ps[FT_G];
+    int nph[FT_G];
+    int E[FT_G];
+    int bad;
+};
+
+// Ring of bulk copies: `n` counts copies issued (thread 0) or consumed (all threads);
+// copy n lands in stage n % FT_NSTAGE, completing that stage's barrier phase n / FT_NSTAGE.
+struct ring {
+    uint32_t n = 0, stage = 0, parity = 0;
+    __device__ void next() {
+        ++n;
+        if (++stage == FT_NSTAGE) {
+            stage = 0;
+            parity ^= 1u;
+        }
+    }
+};
+
+// Fold one sub-group of GS periods [g0, g0 + GS) whose table is built: offsets relative
+// to the epoch's strip start, d[e][gg] = o_e(g) - tmin[e] (FT_SENT: no cell),
+// tmin[e], tlen[e] (strip spread) and full[e] (every period has a cell at epoch e).
+// Returns false if a bulk copy timed out (the block must stop).
+template <int GS>
+__device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab, int Es, int g0,
+                              int k0, const float2 *__restrict__ ab, int I, int64_t ld, int J,
+                              const double *__restrict__ durations,
+                              const uint8_t *__restrict__ mask, ring &iss, ring &con,
+                              int *__restrict__ status) {
+    const int t = threadIdx.x;
+    const int32_t *d = tab;
+    const int32_t *tmin = tab + Es * GS;
+    const int32_t *tlen = tmin + Es;
+    const int32_t *full = tlen + Es;
+    int nph_sub = 0;
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) nph_sub = max(nph_sub, sm.nph[g0 + gg]);
+    float best_lr[GS];
+    uint32_t best_at[GS];
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        best_lr[gg] = -1.0f;
+        best_at[gg] = 0u;
+    }
+    for (int j = 0; j < J && nph_sub > 0; ++j) {
+        const double D = durations[j];
+        unsigned use = 0u;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            const int g = g0 + gg;
+            if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(k0 + g) * J + j]))
+                use |= 1u << gg;
+        }
+        if (!use) continue;
+        const bool all_used = use == (1u << GS) - 1u;
+        const float2 *row = ab + (int64_t)j * ld;
+        for (int i0 = 0; i0 < nph_sub; i0 += FT_T) {
+            float2 acc[GS][FT_R];
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+            auto live = [&](int e) { return e < Es && i0 + tmin[e] < I; };
+            auto issue = [&](int e) {
+                const int a = (i0 + tmin[e]) & ~1;
+                const int len = ((i0 + tmin[e] + tlen[e] + FT_T - a) + 1) & ~1;
+                const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
+                fence_proxy_async();
+                mbar_expect_tx(&sm.bar[iss.stage], bytes);
+                bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
+                iss.next();
+            };
+            if (t == 0)
+                for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
+            for (int e = 0; live(e); ++e) {
+                if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
+                const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
+                const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
+                con.next();
+                const int32_t *de = d + e * GS;
+                if (all_used && full[e]) {
+#pragma unroll
+                    for (int gg = 0; gg < GS; ++gg) {
+                        const float2 *src = S + de[gg];
+                        float2 v[FT_R];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int gg = 0; gg < GS; ++gg) {
+                        const int32_t dg = de[gg];
+                        if (dg == FT_SENT || !((use >> gg) & 1u)) continue;
+                        const float2 *src = S + dg;
+                        float2 v[FT_R];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                    }
+                }
+                if (__syncthreads_or(!ok)) {
+                    // a copy did not land in time: record it, drain the ring, stop
+                    if (t == 0) {
+                        atomicExch(status, CETRA_ETIMEOUT);
+                        while (con.n < iss.n) {
+                            mbar_wait(&sm.bar[con.stage], con.parity);
+                            con.next();
+                        }
+                    }
+                    return false;
+                }
+            }
+            // LR = SA^2 / (2 SB) per (period, phase); the running max keeps the first
+            // (smallest j, then smallest i) of equal values
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg) {
+                if (!((use >> gg) & 1u)) continue;
+                const int nph = sm.nph[g0 + gg];
+#pragma unroll
+                for (int r = 0; r < FT_R; ++r) {
+                    const int i = i0 + t + r * FT_THREADS;
+                    const float2 v = acc[gg][r];
+                    const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
+                    if (i < nph && v.y > 0.0f && lr > best_lr[gg]) {
+                        best_lr[gg] = lr;
+                        best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)i;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg)
+        if (best_lr[gg] >= 0.0f) {
+            const unsigned long long key = make_key(best_lr[gg], best_at[gg]);
+            if (key > sm.best[g0 + gg][t]) sm.best[g0 + gg][t] = key;
+        }
+    return true;
+}
+
+// One period whose offsets do not fit the table: straight from global memory.
+__device__ void fold_direct(fold_smem &sm, int g, int k, const float2 *__restrict__ ab, int I,
+                            int64_t ld, int J, const double *__restrict__ durations,
+                            const uint8_t *__restrict__ mask) {
+    const int t = threadIdx.x;
+    const double Ps = sm.Ps[g];
+    for (int j = 0; j < J; ++j) {
+        if (!(durations[j] < sm.P[g])) continue;
+        if (mask && !mask[(int64_t)k * J + j]) continue;
+        const float2 *row = ab + (int64_t)j * ld;
+        for (int i = t; i < sm.nph[g]; i += blockDim.x) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int64_t e = 0;; ++e) {
+                const int64_t cell = i + epoch_offset(e, Ps);
+                if (cell >= I) break;
+                add2(acc, row[cell]);
+            }
+            if (acc.y > 0.0f) {
+                const float lr = 0.5f * (acc.x * __fdividef(acc.x, acc.y));
+                const unsigned long long key = make_key(lr, (uint32_t)j * (uint32_t)I + (uint32_t)i);
+                if (key > sm.best[g][t]) sm.best[g][t] = key;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
-fold_tma_kernel(const float2 *__restrict__ ab, int64_t I, int64_t ld, int J,
+fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
                 const double *__restrict__ durations, const double *__restrict__ periods, int K,
                 const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q,
                 unsigned long long *__restrict__ keys, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *strips = reinterpret_cast<float2 *>(smem_raw);                      // [NSTAGE][STRIP]
     int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);  // FT_TABLE
-    __shared__ __align__(8) uint64_t bar[FT_NSTAGE];
-    __shared__ unsigned long long red[FT_THREADS / 32];
-    __shared__ unsigned long long s_best[FT_G][FT_THREADS];
-    __shared__ double s_P[FT_G], s_Ps[FT_G];
-    __shared__ int64_t s_nph[FT_G];
-    __shared__ int s_E[FT_G];
-    __shared__ int s_bad;
+    __shared__ fold_smem sm;
 
     const int t = threadIdx.x;
     if (t == 0) {
-        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&bar[st], 1);
+        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t issued = 0, consumed = 0;  // bulk copies issued (thread 0) / waited (all threads)
+    ring iss, con;
 
     const int ngroups = (K + FT_G - 1) / FT_G;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -300,38 +468,37 @@ fold_tma_kernel(const float2 *__restrict__ ab, int64_t I, int64_t ld, int J,
         if (t < FT_G) {
             const int k = k0 + t;
             double P = 0.0, Ps = 0.0;
-            int64_t nph = 0;
-            int E = 0;
+            int nph = 0, E = 0;
             if (k < K) {
                 P = periods[k];
                 Ps = period_steps(P, c, p, q);
                 // a period shorter than one t0 step (or not finite) has no distinct phase: null
                 if (Ps >= 1.0 && isfinite(Ps)) {
                     const double cph = ceil(Ps);
-                    nph = cph < (double)I ? (int64_t)cph : I;
+                    nph = cph < (double)I ? (int)cph : I;
                     const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
                     E = eb < 2147483647.0 ? (int)eb : 2147483647;
                 }
             }
-            s_P[t] = P;
-            s_Ps[t] = Ps;
-            s_nph[t] = nph;
-            s_E[t] = E;
+            sm.P[t] = P;
+            sm.Ps[t] = Ps;
+            sm.nph[t] = nph;
+            sm.E[t] = E;
         }
-        for (int g = 0; g < FT_G; ++g) s_best[g][t] = 0ull;
+        for (int g = 0; g < FT_G; ++g) sm.best[g][t] = 0ull;
         __syncthreads();
 
         for (int g0 = 0; g0 < FT_G;) {
-            // ---- choose the sub-group [g0, g0 + Gs) and build its offset table
+            // choose the sub-group [g0, g0 + Gs) and build its table:
+            // d [Es][Gs], tmin [Es], tlen [Es], full [Es]
             int Gs = FT_G;
             while (g0 % Gs) Gs >>= 1;
             int Es = 0;
             bool table_ok = false;
             for (;;) {
                 Es = 0;
-                for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, s_E[g]);
-                // table: offsets [e][Gs], then min offset [e], then strip length [e]
-                if ((int64_t)Es * (Gs + 2) > FT_TABLE) {
+                for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, sm.E[g]);
+                if ((int64_t)Es * (Gs + 3) > FT_TABLE) {
                     if (Gs > 1) {
                         Gs >>= 1;
                         continue;
@@ -339,148 +506,62 @@ fold_tma_kernel(const float2 *__restrict__ ab, int64_t I, int64_t ld, int J,
                     break;  // a single period with too many epochs: no table
                 }
                 __syncthreads();
-                if (t == 0) s_bad = 0;
-                for (int idx = t; idx < Es * Gs; idx += blockDim.x) {
-                    const int e = idx / Gs, g = g0 + idx % Gs;
-                    int32_t o = FT_SENT;
-                    if (e < s_E[g]) {
-                        const int64_t v = epoch_offset(e, s_Ps[g]);
-                        if (v < I) o = (int32_t)v;
-                    }
-                    tab[idx] = o;
-                }
-                __syncthreads();
-                int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es;
+                if (t == 0) sm.bad = 0;
+                int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es, *full = tlen + Es;
                 bool bad = false;
                 for (int e = t; e < Es; e += blockDim.x) {
-                    int32_t mn = FT_SENT, mx = -1;
+                    int32_t o[FT_G];
+                    int32_t mn = FT_SENT, mx = -1, nvalid = 0;
                     for (int gg = 0; gg < Gs; ++gg) {
-                        const int32_t o = tab[e * Gs + gg];
-                        if (o != FT_SENT) {
-                            mn = min(mn, o);
-                            mx = max(mx, o);
+                        const int g = g0 + gg;
+                        o[gg] = FT_SENT;
+                        if (e < sm.E[g]) {
+                            const int64_t v = epoch_offset(e, sm.Ps[g]);
+                            if (v < I) o[gg] = (int32_t)v;
+                        }
+                        if (o[gg] != FT_SENT) {
+                            mn = min(mn, o[gg]);
+                            mx = max(mx, o[gg]);
+                            ++nvalid;
                         }
                     }
+                    for (int gg = 0; gg < Gs; ++gg)
+                        tab[e * Gs + gg] = o[gg] == FT_SENT ? FT_SENT : o[gg] - mn;
                     tmin[e] = mn;
                     tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
+                    full[e] = nvalid == Gs;
                     if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
                 }
-                if (bad) s_bad = 1;
+                if (bad) sm.bad = 1;
                 __syncthreads();
-                if (s_bad && Gs > 1) {
+                if (sm.bad && Gs > 1) {
                     Gs >>= 1;
                     continue;
                 }
-                table_ok = !s_bad;
+                table_ok = !sm.bad;
                 break;
             }
-            const int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es;
-            int64_t nph_sub = 0;
-            for (int g = g0; g < g0 + Gs; ++g) nph_sub = max(nph_sub, s_nph[g]);
-
-            for (int j = 0; j < J && nph_sub > 0; ++j) {
-                const double D = durations[j];
-                unsigned use = 0u;
-                for (int gg = 0; gg < Gs; ++gg) {
-                    const int g = g0 + gg;
-                    if (s_E[g] > 0 && D < s_P[g] && (!mask || mask[(int64_t)(k0 + g) * J + j]))
-                        use |= 1u << gg;
-                }
-                if (!use) continue;
-                const float2 *row = ab + (int64_t)j * ld;
-
-                if (!table_ok) {
-                    // one period, offsets on the fly (FP64), straight from global memory
-                    const double Ps = s_Ps[g0];
-                    for (int64_t i = t; i < s_nph[g0]; i += blockDim.x) {
-                        float2 acc = make_float2(0.f, 0.f);
-                        for (int64_t e = 0;; ++e) {
-                            const int64_t cell = i + epoch_offset(e, Ps);
-                            if (cell >= I) break;
-                            add2(acc, row[cell]);
-                        }
-                        if (acc.y > 0.0f) {
-                            const float lr = 0.5f * (acc.x * (acc.x / acc.y));
-                            const unsigned long long key =
-                                make_key(lr, (uint32_t)((int64_t)j * I + i));
-                            if (key > s_best[g0][t]) s_best[g0][t] = key;
-                        }
-                    }
-                    continue;
-                }
-
-                for (int64_t i0 = 0; i0 < nph_sub; i0 += FT_T) {
-                    float2 acc[FT_G][FT_R];
-#pragma unroll
-                    for (int gg = 0; gg < FT_G; ++gg)
-#pragma unroll
-                        for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
-                    // epochs of this tile: a prefix (min offsets grow with e)
-                    auto live = [&](int e) { return e < Es && i0 + (int64_t)tmin[e] < I; };
-                    auto issue = [&](int e) {
-                        const int st = issued % FT_NSTAGE;
-                        const int64_t a = (i0 + (int64_t)tmin[e]) & ~(int64_t)1;
-                        int64_t len = i0 + (int64_t)tmin[e] + tlen[e] + FT_T - a;
-                        len = (len + 1) & ~(int64_t)1;
-                        const uint32_t bytes = (uint32_t)(len * (int64_t)sizeof(float2));
-                        fence_proxy_async();
-                        mbar_expect_tx(&bar[st], bytes);
-                        bulk_load(strips + st * FT_STRIP, row + a, bytes, &bar[st]);
-                        ++issued;
-                    };
-                    if (t == 0)
-                        for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
-                    for (int e = 0; live(e); ++e) {
-                        if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
-                        const int st = consumed % FT_NSTAGE;
-                        const bool ok = mbar_wait(&bar[st], (consumed / FT_NSTAGE) & 1u);
-                        ++consumed;
-                        const float2 *S = strips + st * FT_STRIP;
-                        const int64_t a = (i0 + (int64_t)tmin[e]) & ~(int64_t)1;
-#pragma unroll
-                        for (int gg = 0; gg < FT_G; ++gg) {
-                            if (gg >= Gs || !((use >> gg) & 1u)) continue;
-                            const int32_t o = tab[e * Gs + gg];
-                            if (o == FT_SENT) continue;
-                            const float2 *src = S + (i0 + o - a) + t;
-#pragma unroll
-                            for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], src[r * FT_THREADS]);
-                        }
-                        if (__syncthreads_or(!ok)) {
-                            // a copy did not land in time: record it, drain, stop
-                            if (t == 0) {
-                                atomicExch(status, CETRA_ETIMEOUT);
-                                while (consumed < issued) {
-                                    mbar_wait(&bar[consumed % FT_NSTAGE],
-                                              (consumed / FT_NSTAGE) & 1u);
-                                    ++consumed;
-                                }
-                            }
-                            return;
-                        }
-                    }
-#pragma unroll
-                    for (int gg = 0; gg < FT_G; ++gg) {
-                        if (gg >= Gs || !((use >> gg) & 1u)) continue;
-                        const int g = g0 + gg;
-#pragma unroll
-                        for (int r = 0; r < FT_R; ++r) {
-                            const int64_t i = i0 + t + r * FT_THREADS;
-                            const float2 v = acc[gg][r];
-                            if (i < s_nph[g] && v.y > 0.0f) {
-                                const float lr = 0.5f * (v.x * (v.x / v.y));
-                                const unsigned long long key =
-                                    make_key(lr, (uint32_t)((int64_t)j * I + i));
-                                if (key > s_best[g][t]) s_best[g][t] = key;
-                            }
-                        }
-                    }
-                }
+            bool ok = true;
+            if (!table_ok) {
+                fold_direct(sm, g0, k0 + g0, ab, I, ld, J, durations, mask);
+            } else if (Gs == 8) {
+                ok = fold_subgroup<8>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                                      iss, con, status);
+            } else if (Gs == 4) {
+                ok = fold_subgroup<4>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                                      iss, con, status);
+            } else if (Gs == 2) {
+                ok = fold_subgroup<2>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                                      iss, con, status);
+            } else {
+                ok = fold_subgroup<1>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                                      iss, con, status);
             }
+            if (!ok) return;  // uniform: every thread saw the same vote
             g0 += Gs;
         }
         for (int g = 0; g < FT_G; ++g) {
-            const unsigned long long v = block_max_key(s_best[g][t], red);
+            const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
             if (t == 0 && k0 + g < K) keys[k0 + g] = v;
         }
     }
@@ -632,7 +713,7 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
     const int ngroups = (K + FT_G - 1) / FT_G;
     prof_mark(ctx, KID_FOLD, true);
     fold_tma_kernel<<<ngroups, FT_THREADS, fold_smem_bytes(), ctx->stream>>>(
-        ab, plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
+        ab, (int)plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
         plan->cadence, plan->p, plan->q, keys, status);
     prof_mark(ctx, KID_FOLD, false);
     ctx->launches++;

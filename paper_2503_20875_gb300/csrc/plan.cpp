@@ -139,7 +139,8 @@ int plan_build(cetra_ctx *ctx, const cetra_params *params, const double *time, c
     plan->flux_is_offset = params->flux_is_offset ? 1 : 0;
     plan->precision = params->precision;
     plan->durations.assign(durations, durations + n_dur);
-    if (plan->n_grid > (int64_t)INT32_MAX / 2 || plan->n_t0 * (int64_t)n_dur > (int64_t)UINT32_MAX)
+    if (plan->n_grid > (int64_t)INT32_MAX / 2 || plan->n_t0 > (int64_t)INT32_MAX / 2 ||
+        plan->n_t0 * (int64_t)n_dur > (int64_t)UINT32_MAX)
         return set_error(ctx, CETRA_EINVAL, "plan: grid too large (n_dur * n_t0 must fit 32 bits)");
     plan->ab_ld = ((plan->n_t0 + FOLD_PAD) + 1) & ~(int64_t)1;
     if (!with_tables) return CETRA_OK;
