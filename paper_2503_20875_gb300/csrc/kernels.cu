@@ -336,7 +336,8 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
             for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
                 for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
-            auto live = [&](int e) { return e < Es && i0 + tmin[e] < I; };
+            // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
+            auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
             auto issue = [&](int e) {
                 const int a = (i0 + tmin[e]) & ~1;
                 const int len = ((i0 + tmin[e] + tlen[e] + FT_T - a) + 1) & ~1;
