@@ -191,6 +191,34 @@ int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_worksp
                           int64_t *d_i, int32_t *d_j);
 
 /*
+ * Allocation-free variant of cetra_periodic_device (the paper has no
+ * counterpart; this is a deployment aid). For callers that cannot allocate
+ * device memory while they run: a fixed memory pool, device buffers handed in
+ * by a host application with its own allocator, or a workspace sized once for
+ * the linear grid (n_periods = 0) and then reused for period grids of any
+ * length. The fold's per-period keys and status word live in a static device
+ * array inside the library (CETRA_STATIC_MAX_PERIODS keys + 256 B, about
+ * 2 MiB, held by every GPU that loads the library until the process exits)
+ * instead of in d_workspace, so d_workspace needs only
+ * cetra_workspace_bytes(plan, 0) bytes and must hold a linear grid from
+ * cetra_linear_device. Arguments, outputs and tie rules are those of
+ * cetra_periodic_device. The call allocates nothing; its first call on a
+ * device looks up the array's device address (make that first call before
+ * any stream capture). Calls on one device share the array: calls whose
+ * kernels overlap on the GPU race and must be serialised by the caller. The
+ * status word is cleared at the start of every call; read it back with a
+ * stream synchronisation if needed (a timed-out fold leaves NaN outputs).
+ * Errors: CETRA_ECAPACITY (n_periods > CETRA_STATIC_MAX_PERIODS, or the
+ * workspace is smaller than the linear grid), CETRA_EINVAL, CETRA_ECUDA.
+ */
+#define CETRA_STATIC_MAX_PERIODS 262144
+int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                                 size_t workspace_bytes, const double *d_periods, int n_periods,
+                                 const uint8_t *d_mask, double *d_dlogl, double *d_t0,
+                                 double *d_duration, double *d_depth, double *d_depth_var,
+                                 int64_t *d_i, int32_t *d_j);
+
+/*
  * Status word of a workspace after cetra_periodic_device: 0, or CETRA_ETIMEOUT
  * if a bounded device-side wait of the fold gave up (its outputs are then NaN).
  * Synchronises the context's stream.

@@ -75,6 +75,8 @@ SIGNATURES = {
                                      _P]),
     "cetra_logl0_device": (_INT, [_P, _P, _P, _SZ, _P]),
     "cetra_workspace_status": (_INT, [_P, _P, _P, _SZ, ctypes.POINTER(_INT)]),
+    "cetra_periodic_device_static": (_INT, [_P, _P, _P, _SZ, _P, _INT, _P, _P, _P, _P, _P, _P,
+                                            _P, _P]),
     "cetra_linear_search": (_INT, [_P, ctypes.POINTER(cetra_params), _P, _P, _P, _I64, _P, _INT,
                                    _P, _INT, ctypes.POINTER(_P), _P, _P, _P,
                                    ctypes.POINTER(_I64)]),
