@@ -90,7 +90,8 @@ constexpr int FT_THREADS = 256;
 constexpr int FT_T = FT_THREADS * FT_R;  // phases per tile
 constexpr int FT_G = 8;                  // periods per block
 constexpr int FT_TABLE = 8192;           // epoch-offset table entries (32 KiB)
-constexpr uint32_t FT_SPIN_LIMIT = 1u << 21;  // polls of a bulk-copy barrier before giving up
+constexpr long long FT_WAIT_CYCLES = 2000000000ll;  // ~1 s of SM clocks before a wait gives up
+constexpr uint32_t FT_SUSPEND_NS = 20000;            // suspend hint of one barrier try
 constexpr int FOLD_PAD = FT_STRIP + 16;  // zero cells after each grid row
 size_t fold_smem_bytes();
 

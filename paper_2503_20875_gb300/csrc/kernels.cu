@@ -41,9 +41,14 @@ __device__ __forceinline__ void fma2(float2 &acc, float2 a, float2 b) {
 
 // acc += v elementwise with one packed FP32x2 add.
 __device__ __forceinline__ void add2(float2 &acc, float2 v) {
+#ifdef CETRA_SCALAR_ADD
+    acc.x += v.x;
+    acc.y += v.y;
+#else
     unsigned long long d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(acc)), "l"(pack2(v)));
     acc = unpack2(d);
+#endif
 }
 
 // Nearest epoch cell offset o_e = floor(e Ps + 1/2), FP64, no contraction.
@@ -233,24 +238,26 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ bool mbar_done(uint64_t *bar, uint32_t parity) {
+// Potentially blocking test of a barrier phase: the thread may be suspended (up
+// to the hinted time) instead of spinning, so waiting warps do not take issue slots.
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(FT_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the phase did not complete within FT_SPIN_LIMIT polls
-// (non-blocking polls with a short back-off: well under a second in total).
+// Bounded wait: false if the phase did not complete within FT_WAIT_CYCLES SM clocks.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < FT_SPIN_LIMIT; ++it) {
-        if (mbar_done(bar, parity)) return true;
-        if (it >= 32) __nanosleep(64);
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > FT_WAIT_CYCLES) return false;
     }
-    return false;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -292,6 +299,24 @@ struct ring {
         }
     }
 };
+
+// The GS strip offsets of one epoch, with 16-byte shared loads where the row allows.
+template <int GS>
+__device__ __forceinline__ void load_offsets(const int32_t *de, int32_t *dv) {
+    if constexpr (GS % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < GS / 4; ++v) {
+            const int4 x = reinterpret_cast<const int4 *>(de)[v];
+            dv[4 * v] = x.x;
+            dv[4 * v + 1] = x.y;
+            dv[4 * v + 2] = x.z;
+            dv[4 * v + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) dv[gg] = de[gg];
+    }
+}
 
 // Fold one sub-group of GS periods [g0, g0 + GS) whose table is built: offsets relative
 // to the epoch's strip start, d[e][gg] = o_e(g) - tmin[e] (FT_SENT: no cell),
@@ -356,9 +381,11 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                 con.next();
                 const int32_t *de = d + e * GS;
                 if (all_used && full[e]) {
+                    int32_t dv[GS];
+                    load_offsets<GS>(de, dv);
 #pragma unroll
                     for (int gg = 0; gg < GS; ++gg) {
-                        const float2 *src = S + de[gg];
+                        const float2 *src = S + dv[gg];
                         float2 v[FT_R];
 #pragma unroll
                         for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
