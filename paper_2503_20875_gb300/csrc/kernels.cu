@@ -300,32 +300,6 @@ struct ring {
     }
 };
 
-// One (A, B) cell of a shared strip as a packed 64-bit value, at byte address
-// `addr + OFF` of the shared window. Volatile: it must stay after the barrier wait.
-template <int OFF>
-__device__ __forceinline__ unsigned long long lds_cell(uint32_t addr) {
-    unsigned long long v;
-    asm volatile("ld.shared.b64 %0, [%1+%2];" : "=l"(v) : "r"(addr), "n"(OFF));
-    return v;
-}
-// The FT_R cells of one thread (stride FT_THREADS cells) from byte address `a`.
-template <int R>
-__device__ __forceinline__ void lds_cells(uint32_t a, unsigned long long *v) {
-    v[0] = lds_cell<0>(a);
-    if constexpr (R > 1) v[1] = lds_cell<1 * FT_THREADS * 8>(a);
-    if constexpr (R > 2) v[2] = lds_cell<2 * FT_THREADS * 8>(a);
-    if constexpr (R > 3) v[3] = lds_cell<3 * FT_THREADS * 8>(a);
-    if constexpr (R > 4) v[4] = lds_cell<4 * FT_THREADS * 8>(a);
-    if constexpr (R > 5) v[5] = lds_cell<5 * FT_THREADS * 8>(a);
-    if constexpr (R > 6) v[6] = lds_cell<6 * FT_THREADS * 8>(a);
-    if constexpr (R > 7) v[7] = lds_cell<7 * FT_THREADS * 8>(a);
-    static_assert(R <= 8, "at most 8 phases per thread");
-}
-// acc += v on packed (A, B) pairs.
-__device__ __forceinline__ void add_packed(unsigned long long &acc, unsigned long long v) {
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(v));
-}
-
 // The GS strip offsets of one epoch, with 16-byte shared loads where the row allows.
 template <int GS>
 __device__ __forceinline__ void load_offsets(const int32_t *de, int32_t *dv) {
@@ -382,11 +356,11 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
         const bool all_used = use == (1u << GS) - 1u;
         const float2 *row = ab + (int64_t)j * ld;
         for (int i0 = 0; i0 < nph_sub; i0 += FT_T) {
-            unsigned long long acc[GS][FT_R];  // packed (SA, SB) per (period, phase)
+            float2 acc[GS][FT_R];
 #pragma unroll
             for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-                for (int r = 0; r < FT_R; ++r) acc[gg][r] = 0ull;
+                for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
             // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
             auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
             auto issue = [&](int e) {
@@ -403,24 +377,33 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
             for (int e = 0; live(e); ++e) {
                 if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
                 const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
-                // shared byte address of this thread's first cell in the epoch's strip
-                const uint32_t sb =
-                    smem_u32(strips) +
-                    (uint32_t)(con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t) *
-                        (uint32_t)sizeof(float2);
+                const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
                 con.next();
                 const int32_t *de = d + e * GS;
-                int32_t dv[GS];
-                load_offsets<GS>(de, dv);
-                const bool fast = all_used && full[e];
+                if (all_used && full[e]) {
+                    int32_t dv[GS];
+                    load_offsets<GS>(de, dv);
 #pragma unroll
-                for (int gg = 0; gg < GS; ++gg) {
-                    if (!fast && (dv[gg] == FT_SENT || !((use >> gg) & 1u))) continue;
-                    const uint32_t a = sb + (uint32_t)dv[gg] * (uint32_t)sizeof(float2);
-                    unsigned long long v[FT_R];
-                    lds_cells<FT_R>(a, v);
+                    for (int gg = 0; gg < GS; ++gg) {
+                        const float2 *src = S + dv[gg];
+                        float2 v[FT_R];
 #pragma unroll
-                    for (int r = 0; r < FT_R; ++r) add_packed(acc[gg][r], v[r]);
+                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int gg = 0; gg < GS; ++gg) {
+                        const int32_t dg = de[gg];
+                        if (dg == FT_SENT || !((use >> gg) & 1u)) continue;
+                        const float2 *src = S + dg;
+                        float2 v[FT_R];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+#pragma unroll
+                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                    }
                 }
                 if (__syncthreads_or(!ok)) {
                     // a copy did not land in time: record it, drain the ring, stop
@@ -443,7 +426,7 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
 #pragma unroll
                 for (int r = 0; r < FT_R; ++r) {
                     const int i = i0 + t + r * FT_THREADS;
-                    const float2 v = unpack2(acc[gg][r]);
+                    const float2 v = acc[gg][r];
                     const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
                     if (i < nph && v.y > 0.0f && lr > best_lr[gg]) {
                         best_lr[gg] = lr;
