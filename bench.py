@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-fold-stride", type=int, default=25,
                     help="period stride of the oracle's fold sample")
+    ap.add_argument("--period-range", default=None,
+                    help="a:b, search only periods[a:b] of the workload (profiling a small case)")
     return ap.parse_args()
 
 
@@ -204,6 +206,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     w = synth.make_workload(args.workload, seed=1 + rank)
+    if args.period_range:
+        a, b = (int(x) for x in args.period_range.split(":"))
+        w.periods = w.periods[a:b]
     ctx = cetra.Context(local, stream=stream)
     plan = cetra.Plan(ctx, w.time, w.flux, w.flux_err, w.durations, w.template,
                       cadence=w.cadence, t0_step=w.t0_step)
