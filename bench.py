@@ -36,6 +36,9 @@ sys.path.insert(0, ROOT)
 METRIC = "light curves searched/s on 1 GB300 vs plain form; % FMA/HBM peak; ΔlogL rel err"
 UNIT = "curves/s"
 FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one fold launch (ncu capture of this kernel
+# version); None once the kernel changes
+FOLD_DRAM_BYTES = {"tess_20s_27d": 20092160}
 
 
 def parse():
@@ -291,8 +294,10 @@ def main():
     fold_bytes = 8.0 * cells
     achieved = fold_bytes / (fold_ms_per * 1e-3) / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    roofline = {"bound": "hbm", "kernel": "fold_kernel", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+    # DRAM bytes of one full fold launch of this workload (ncu, profiles/fold_tma_kernel_tess_20s_27d.md)
+    traffic = FOLD_DRAM_BYTES.get(args.workload) if not args.period_range else None
+    roofline = {"bound": "hbm", "kernel": "fold_tma_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "algorithmic_bytes_per_launch": fold_bytes, "cell_reads_per_launch": cells,
                 "ms_per_launch": fold_ms_per}
@@ -302,7 +307,7 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = (peaks or {}).get("sm_max_mhz", 2070.0)
     fma_peak = sm_count * 128 * 2 * clk * 1e6 / 1e12
-    roofline_linear = {"bound": "alu", "kernel": "linear_kernel",
+    roofline_linear = {"bound": "alu", "kernel": "linear_kernel<9>",
                        "achieved": lin_fl / (lin_ms_per * 1e-3) / 1e12, "peak": fma_peak,
                        "unit": "TFLOP/s", "frac": lin_fl / (lin_ms_per * 1e-3) / 1e12 / fma_peak,
                        "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 x {clk:.0f} MHz",
