@@ -220,3 +220,22 @@ def test_full_tess_20s_27d_sampled_periods():
     ps = compare_periodic(g_sel, o, w.periods[sel])
     print("tess_20s_27d", ls, ps)
     assert abs(w.periods[kbest] - 11.3) / 11.3 < 0.01 or abs(w.periods[kbest] - 5.1) / 5.1 < 0.01
+
+
+def test_full_kepler_1min_4yr_sampled_periods():
+    """4-yr baseline at 1-min cadence (2.1 M points, absolute times + 2.45e6 d),
+    30 durations: the whole linear grid; the fold on every 1000th period plus the
+    41 periods around the injected 365-d transit. Multi-year tolerance 1e-4."""
+    w = synth.make_workload("kepler_1min_4yr")
+    k365 = int(np.argmin(np.abs(w.periods - 365.0)))
+    sel = np.unique(np.concatenate([np.arange(0, w.periods.size, 1000),
+                                    np.arange(k365 - 20, k365 + 21)]))
+    P = w.periods[sel]
+    g = gpu_search(w.time, w.flux, w.flux_err, w.durations, w.template, P, cadence=w.cadence,
+                   t0_step=w.t0_step)
+    o = oracle_search(w.time, w.flux, w.flux_err, w.durations, w.template, P,
+                      cadence=w.cadence, t0_step=w.t0_step)
+    _check_geometry(g, o)
+    ls = compare_linear(g, o, w.durations, r_flat=1e-4)
+    ps = compare_periodic(g, o, P, r_flat=1e-4, r_low=1e-3)
+    print("kepler_1min_4yr", ls, ps)
