@@ -198,9 +198,7 @@ int cetra_plan_create(cetra_ctx *ctx, const cetra_params *params, const double *
     cetra_params def;
     cetra_params_default(&def);
     if (!params) params = &def;
-    if (params->precision == CETRA_FP32_KAHAN)
-        return set_error(ctx, CETRA_EINVAL, "plan: CETRA_FP32_KAHAN is not available in this build");
-    if (params->precision != CETRA_FP32)
+    if (params->precision != CETRA_FP32 && params->precision != CETRA_FP32_KAHAN)
         return set_error(ctx, CETRA_EINVAL, "plan: unknown precision");
     device_guard g(ctx->device);
     cetra_plan *plan = new (std::nothrow) cetra_plan;

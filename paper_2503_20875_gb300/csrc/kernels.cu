@@ -51,6 +51,34 @@ __device__ __forceinline__ void add2(float2 &acc, float2 v) {
 #endif
 }
 
+// d = a - b elementwise with one packed FP32x2 subtract.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(d);
+}
+
+// Kahan-compensated s += a * b on (A, B) pairs; nc carries minus the running
+// compensation: y = a b + nc, t = s + y, nc = y - (t - s), s = t.
+__device__ __forceinline__ void kahan_fma2(float2 &s, float2 &nc, float2 a, float2 b) {
+    float2 y = nc;
+    fma2(y, a, b);
+    float2 t = s;
+    add2(t, y);
+    nc = sub2(y, sub2(t, s));
+    s = t;
+}
+
+// Kahan-compensated s += v on (A, B) pairs (nc as above).
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &nc, float2 v) {
+    float2 y = v;
+    add2(y, nc);
+    float2 t = s;
+    add2(t, y);
+    nc = sub2(y, sub2(t, s));
+    s = t;
+}
+
 // Nearest epoch cell offset o_e = floor(e Ps + 1/2), FP64, no contraction.
 __device__ __forceinline__ int64_t epoch_offset(int64_t e, double Ps) {
     return (int64_t)floor(__dadd_rn(__dmul_rn((double)e, Ps), 0.5));
@@ -92,7 +120,8 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
 // matching span of the (W y, W) grid in shared memory; each thread slides a register
 // window over the span and accumulates RB outputs (A, B) with packed FP32x2 FMAs.
 // For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
-template <int RB>
+// KAHAN: every term is added with Kahan compensation (CETRA_FP32_KAHAN).
+template <int RB, bool KAHAN>
 __global__ void __launch_bounds__(128)
 linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
@@ -118,6 +147,7 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
     // Blocked summation: `acc` collects at most LIN_SUB * RB terms before it is
     // folded into `tot`, so the FP32 rounding error grows with the block length
     // plus the number of blocks instead of with the window length.
+    // With KAHAN, `tot` holds minus the compensation of `acc` instead.
     float2 acc[RB], tot[RB];
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) acc[rr] = tot[rr] = make_float2(0.f, 0.f);
@@ -150,20 +180,32 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
                         const int k1 = kb + s;
                         const float2 mm = M[p * k1];
 #pragma unroll
-                        for (int rr = 0; rr < RB; ++rr) fma2(acc[rr], mm, buf[(s + rr) % RB]);
+                        for (int rr = 0; rr < RB; ++rr) {
+                            if constexpr (KAHAN)
+                                kahan_fma2(acc[rr], tot[rr], mm, buf[(s + rr) % RB]);
+                            else
+                                fma2(acc[rr], mm, buf[(s + rr) % RB]);
+                        }
                         buf[s] = V[p * (k1 + RB)];
                     }
                 }
+                if constexpr (!KAHAN) {
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    add2(tot[rr], acc[rr]);
-                    acc[rr] = make_float2(0.f, 0.f);
+                    for (int rr = 0; rr < RB; ++rr) {
+                        add2(tot[rr], acc[rr]);
+                        acc[rr] = make_float2(0.f, 0.f);
+                    }
                 }
             }
         }
     }
 #pragma unroll
-    for (int rr = 0; rr < RB; ++rr) acc[rr] = tot[rr];
+    for (int rr = 0; rr < RB; ++rr) {
+        if constexpr (KAHAN)
+            add2(acc[rr], tot[rr]);  // fold the last compensation in
+        else
+            acc[rr] = tot[rr];
+    }
 
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
@@ -321,8 +363,9 @@ __device__ __forceinline__ void load_offsets(const int32_t *de, int32_t *dv) {
 // Fold one sub-group of GS periods [g0, g0 + GS) whose table is built: offsets relative
 // to the epoch's strip start, d[e][gg] = o_e(g) - tmin[e] (FT_SENT: no cell),
 // tmin[e], tlen[e] (strip spread) and full[e] (every period has a cell at epoch e).
+// R phases per thread (tile FT_THREADS * R <= FT_T); KAHAN: compensated epoch sums.
 // Returns false if a bulk copy timed out (the block must stop).
-template <int GS>
+template <int GS, int R, bool KAHAN>
 __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab, int Es, int g0,
                               int k0, const float2 *__restrict__ ab, int I, int64_t ld, int J,
                               const double *__restrict__ durations,
@@ -355,17 +398,25 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
         if (!use) continue;
         const bool all_used = use == (1u << GS) - 1u;
         const float2 *row = ab + (int64_t)j * ld;
-        for (int i0 = 0; i0 < nph_sub; i0 += FT_T) {
-            float2 acc[GS][FT_R];
+        constexpr int T = FT_THREADS * R;
+        for (int i0 = 0; i0 < nph_sub; i0 += T) {
+            float2 acc[GS][R];
+            float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
 #pragma unroll
             for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-                for (int r = 0; r < FT_R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+                for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+            if constexpr (KAHAN) {
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+            }
             // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
             auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
             auto issue = [&](int e) {
                 const int a = (i0 + tmin[e]) & ~1;
-                const int len = ((i0 + tmin[e] + tlen[e] + FT_T - a) + 1) & ~1;
+                const int len = ((i0 + tmin[e] + tlen[e] + T - a) + 1) & ~1;
                 const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
                 fence_proxy_async();
                 mbar_expect_tx(&sm.bar[iss.stage], bytes);
@@ -386,11 +437,16 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
 #pragma unroll
                     for (int gg = 0; gg < GS; ++gg) {
                         const float2 *src = S + dv[gg];
-                        float2 v[FT_R];
+                        float2 v[R];
 #pragma unroll
-                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+                        for (int r = 0; r < R; ++r) v[r] = src[r * FT_THREADS];
 #pragma unroll
-                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                        for (int r = 0; r < R; ++r) {
+                            if constexpr (KAHAN)
+                                kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
+                            else
+                                add2(acc[gg][r], v[r]);
+                        }
                     }
                 } else {
 #pragma unroll
@@ -398,11 +454,16 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                         const int32_t dg = de[gg];
                         if (dg == FT_SENT || !((use >> gg) & 1u)) continue;
                         const float2 *src = S + dg;
-                        float2 v[FT_R];
+                        float2 v[R];
 #pragma unroll
-                        for (int r = 0; r < FT_R; ++r) v[r] = src[r * FT_THREADS];
+                        for (int r = 0; r < R; ++r) v[r] = src[r * FT_THREADS];
 #pragma unroll
-                        for (int r = 0; r < FT_R; ++r) add2(acc[gg][r], v[r]);
+                        for (int r = 0; r < R; ++r) {
+                            if constexpr (KAHAN)
+                                kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
+                            else
+                                add2(acc[gg][r], v[r]);
+                        }
                     }
                 }
                 if (__syncthreads_or(!ok)) {
@@ -424,9 +485,10 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                 if (!((use >> gg) & 1u)) continue;
                 const int nph = sm.nph[g0 + gg];
 #pragma unroll
-                for (int r = 0; r < FT_R; ++r) {
+                for (int r = 0; r < R; ++r) {
                     const int i = i0 + t + r * FT_THREADS;
-                    const float2 v = acc[gg][r];
+                    float2 v = acc[gg][r];
+                    if constexpr (KAHAN) add2(v, cmp[gg][r]);
                     const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
                     if (i < nph && v.y > 0.0f && lr > best_lr[gg]) {
                         best_lr[gg] = lr;
@@ -471,6 +533,7 @@ __device__ void fold_direct(fold_smem &sm, int g, int k, const float2 *__restric
     }
 }
 
+template <bool KAHAN>
 __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
 fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
                 const double *__restrict__ durations, const double *__restrict__ periods, int K,
@@ -573,16 +636,16 @@ fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
             if (!table_ok) {
                 fold_direct(sm, g0, k0 + g0, ab, I, ld, J, durations, mask);
             } else if (Gs == 8) {
-                ok = fold_subgroup<8>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                ok = fold_subgroup<8, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
                                       iss, con, status);
             } else if (Gs == 4) {
-                ok = fold_subgroup<4>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                ok = fold_subgroup<4, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
                                       iss, con, status);
             } else if (Gs == 2) {
-                ok = fold_subgroup<2>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                ok = fold_subgroup<2, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
                                       iss, con, status);
             } else {
-                ok = fold_subgroup<1>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
+                ok = fold_subgroup<1, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
                                       iss, con, status);
             }
             if (!ok) return;  // uniform: every thread saw the same vote
@@ -708,13 +771,18 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
     plan->lin_smem = bytes(threads, kc);
     size_t limit = ctx->max_smem_optin ? ctx->max_smem_optin : 227 * 1024;
     if (plan->lin_smem > limit) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(linear_kernel<LIN_RB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)plan->lin_smem);
-    if (e != cudaSuccess) return e;
+    for (auto fn : {linear_kernel<LIN_RB, false>, linear_kernel<LIN_RB, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)plan->lin_smem);
+        if (e != cudaSuccess) return e;
+    }
     // the fold's strip ring and offset table (dynamic) exceed the default 48 KiB
-    return cudaFuncSetAttribute(fold_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fold_smem_bytes());
+    for (auto fn : {fold_tma_kernel<false>, fold_tma_kernel<true>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fold_smem_bytes());
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
@@ -726,7 +794,9 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
     if (gx == 0) return cudaSuccess;
     dim3 grid((unsigned)gx, (unsigned)(plan->J * q));
     prof_mark(ctx, KID_LINEAR, true);
-    linear_kernel<LIN_RB><<<grid, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
+    auto kern = plan->precision == CETRA_FP32_KAHAN ? linear_kernel<LIN_RB, true>
+                                                    : linear_kernel<LIN_RB, false>;
+    kern<<<grid, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
         wy, w, plan->n_grid, plan->d_tables, plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
         (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, ab, depth, var, dlogl);
     prof_mark(ctx, KID_LINEAR, false);
@@ -740,7 +810,8 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
     if (K <= 0) return cudaSuccess;
     const int ngroups = (K + FT_G - 1) / FT_G;
     prof_mark(ctx, KID_FOLD, true);
-    fold_tma_kernel<<<ngroups, FT_THREADS, fold_smem_bytes(), ctx->stream>>>(
+    auto kern = plan->precision == CETRA_FP32_KAHAN ? fold_tma_kernel<true> : fold_tma_kernel<false>;
+    kern<<<ngroups, FT_THREADS, fold_smem_bytes(), ctx->stream>>>(
         ab, (int)plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
         plan->cadence, plan->p, plan->q, keys, status);
     prof_mark(ctx, KID_FOLD, false);

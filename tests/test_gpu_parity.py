@@ -239,3 +239,50 @@ def test_full_kepler_1min_4yr_sampled_periods():
     ls = compare_linear(g, o, w.durations, r_flat=1e-4)
     ps = compare_periodic(g, o, P, r_flat=1e-4, r_low=1e-3)
     print("kepler_1min_4yr", ls, ps)
+
+
+# ----------------------------------------------------------------------------- precision form
+
+
+@pytest.mark.parametrize("name", ["tess_small", "q3_gaps", "p3q20", "long_window"])
+def test_kahan_small_case_parity(name):
+    """CETRA_FP32_KAHAN: compensated window and fold sums, same bounds as plain."""
+    kw = dict(CASES[name])
+    periods = kw.pop("periods")
+    w = custom(seed=11, **kw)
+    args = (w.time, w.flux, w.flux_err, w.durations, w.template, periods)
+    g = gpu_search(*args, cadence=w.cadence, t0_step=w.t0_step, precision="kahan")
+    o = oracle_search(*args, cadence=w.cadence, t0_step=w.t0_step)
+    _check_geometry(g, o)
+    print(name, "kahan", compare_linear(g, o, w.durations), compare_periodic(g, o, periods))
+
+
+def _max_rel(a, b, sel):
+    return float(np.max(np.abs(a[sel].astype(np.float64) - b[sel]) / np.abs(b[sel]), initial=0.0))
+
+
+def test_kahan_vs_plain_error_on_4yr_baseline():
+    """The precision form on the 4-yr workload: both forms meet the bound, and the
+    compensated sums are at least as close to the FP64 oracle as the plain ones."""
+    w = synth.make_workload("kepler_1min_4yr")
+    k365 = int(np.argmin(np.abs(w.periods - 365.0)))
+    P = w.periods[np.unique(np.concatenate([np.arange(0, w.periods.size, 2000),
+                                            np.arange(k365 - 5, k365 + 6)]))]
+    args = (w.time, w.flux, w.flux_err, w.durations, w.template, P)
+    kw = dict(cadence=w.cadence, t0_step=w.t0_step)
+    o = oracle_search(*args, **kw)
+    plain = gpu_search(*args, **kw)
+    kahan = gpu_search(*args, **kw, precision="kahan")
+    sig = ~np.isnan(o["dlogl"]) & (o["dlogl"] >= 25)
+    ok = ~np.isnan(o["dlogl"])
+    report = {}
+    for name, g in (("plain", plain), ("kahan", kahan)):
+        compare_linear(g, o, w.durations, r_flat=1e-4)
+        compare_periodic(g, o, P, r_flat=1e-4, r_low=1e-3)
+        report[name] = {"lin_sig": _max_rel(g["dlogl"], o["dlogl"], sig),
+                        "depth_all": _max_rel(g["depth"], o["depth"], ok & (np.abs(o["depth"]) > 0)),
+                        "per": _max_rel(g["periodic"]["dlogl"], o["periodic"]["dlogl"],
+                                        ~np.isnan(o["periodic"]["dlogl"]))}
+    print("precision form (max relative error vs the FP64 oracle)", report)
+    assert report["kahan"]["lin_sig"] <= report["plain"]["lin_sig"] + 2e-7
+    assert report["kahan"]["per"] <= report["plain"]["per"] + 2e-7
