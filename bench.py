@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-fold-stride", type=int, default=25,
                     help="period stride of the oracle's fold sample")
+    ap.add_argument("--precision", choices=["fp32", "kahan"], default="fp32",
+                    help="plain FP32 sums or the Kahan-compensated precision form")
     ap.add_argument("--period-range", default=None,
                     help="a:b, search only periods[a:b] of the workload (profiling a small case)")
     return ap.parse_args()
@@ -214,7 +216,7 @@ def main():
         w.periods = w.periods[a:b]
     ctx = cetra.Context(local, stream=stream)
     plan = cetra.Plan(ctx, w.time, w.flux, w.flux_err, w.durations, w.template,
-                      cadence=w.cadence, t0_step=w.t0_step)
+                      cadence=w.cadence, t0_step=w.t0_step, precision=args.precision)
     info = plan.info
     ds = cetra.DeviceSearch(ctx, plan, w.periods)
     d_t = torch.as_tensor(w.time, device=dev)
@@ -271,7 +273,7 @@ def main():
         t0 = time.perf_counter()
         grid, _, _, _ = cetra.cetra_linear_search(ctx, h_t, h_f, h_e, w.durations, w.template,
                                                   outputs=False, cadence=w.cadence,
-                                                  t0_step=w.t0_step)
+                                                  t0_step=w.t0_step, precision=args.precision)
         per = cetra.cetra_periodic_search(ctx, grid, h_P)
         best = per["best_k"]
         grid.close()
@@ -295,7 +297,8 @@ def main():
     achieved = fold_bytes / (fold_ms_per * 1e-3) / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     # DRAM bytes of one full fold launch of this workload (ncu, profiles/fold_tma_kernel_tess_20s_27d.md)
-    traffic = FOLD_DRAM_BYTES.get(args.workload) if not args.period_range else None
+    traffic = (FOLD_DRAM_BYTES.get(args.workload)
+               if not args.period_range and args.precision == "fp32" else None)
     roofline = {"bound": "hbm", "kernel": "fold_tma_kernel", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
@@ -317,8 +320,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n_points": int(w.time.size),
-                       "n_grid": int(info["n_grid"]), "n_t0": int(info["n_t0"]),
+            "config": {"workload": args.workload, "precision": args.precision,
+                       "n_points": int(w.time.size), "n_grid": int(info["n_grid"]), "n_t0": int(info["n_t0"]),
                        "n_durations": int(w.durations.size), "n_periods": int(w.periods.size),
                        "cadence_s": w.cadence * 86400, "t0_step_s": w.t0_step * 86400,
                        "template_samples": 1024, "parallelism": f"replicas x{world}",
