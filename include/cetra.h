@@ -262,6 +262,79 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
                           int n_periods, const uint8_t *dur_mask, double *dlogl, double *t0,
                           double *duration, double *depth, double *depth_var, int64_t *best_k);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched form: many light curves of uneven length, each searched with the linear and the
+ * periodic search of Sec. 2.2 and Sec. 2.3, in one launch per stage (a persistent fold
+ * kernel drains a work queue of (curve, 8-period group) items), replayed as a CUDA graph.
+ * Curves share the cadence, the t0 step, the durations and the template; each has its own
+ * time span and its own period grid
+ *     P_k = period_min * ratio^k,  k = 0, 1, ... while P_k <= period_max,
+ * with ratio^k evaluated in FP64 by least-significant-bit-first square-and-multiply
+ * (x = 1, b = ratio; for each bit of k: if set x = x * b; b = b * b).
+ * ------------------------------------------------------------------------------------- */
+typedef struct cetra_batch cetra_batch;
+
+/* Best periodic model of one curve (Sec. 2.3), re-summed in FP64. */
+typedef struct {
+    double dlogl;      /* LR of the best (period, t0, duration); NaN if the curve has none */
+    double period;     /* days */
+    double t0;         /* mid-time of a transit, absolute days */
+    double duration;   /* days */
+    double depth;      /* common depth Z */
+    double depth_var;  /* variance of Z */
+    int64_t k;         /* index in the curve's period grid, -1 if null */
+    int64_t i;         /* t0 index in the curve's own grid, -1 if null */
+    int32_t j;         /* duration index, -1 if null */
+    int32_t n_periods; /* periods searched for this curve */
+} cetra_best;
+
+typedef struct {
+    int32_t n_curves;
+    int32_t n_dur;
+    int64_t n_points;     /* input points (all curves) */
+    int64_t n_cells;      /* resampled cells (all curves) */
+    int64_t n_t0;         /* t0 points (all curves) */
+    int64_t n_periods;    /* periods (all curves) */
+    int64_t n_fold_items; /* (curve, 8-period group) work items of the fold */
+    int64_t fold_cell_reads; /* algorithmic (A, B) reads of the fold */
+    size_t device_bytes;  /* device memory the batch holds */
+    int32_t linear_threads;  /* chosen linear block size */
+    int32_t fold_variant;    /* chosen fold variant (phases per thread, blocks per SM) */
+    int32_t fold_blocks;     /* persistent fold blocks */
+    int32_t graph;           /* 1 once the run is captured as a CUDA graph */
+} cetra_batch_info;
+
+/*
+ * Build a batch: copy the curves to the device, lay out every curve's grids, and (autotune
+ * != 0) time the candidate tile shapes of the linear and fold kernels on this batch and keep
+ * the fastest. offsets: host int64 [n_curves + 1], curve c owns points
+ * [offsets[c], offsets[c+1]) of time (FP64), flux and flux_err (FP32). params->cadence and
+ * params->t0_step must be > 0 (shared by all curves). period_min: host [n_curves], > 0.
+ * period_max: host [n_curves] or NULL (half the curve's time span); ratio: host [n_curves]
+ * or NULL (1 + min(durations) / (2 x time span)), each > 1. The batch owns its device memory
+ * (cetra_batch_destroy). Errors: CETRA_EINVAL, CETRA_ENOMEM, CETRA_ECUDA.
+ */
+int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
+                       const int64_t *offsets, const double *time, const float *flux,
+                       const float *flux_err, const double *durations, int n_dur,
+                       const float *tmpl, int tmpl_len, const double *period_min,
+                       const double *period_max, const double *period_ratio, int autotune,
+                       cetra_batch **batch);
+/* Run the whole search of every curve (captured as a CUDA graph on the first call, replayed
+ * after) and copy the per-curve results to `best` (host [n_curves], may be NULL). Blocks
+ * until done. Errors: CETRA_ECUDA, CETRA_ETIMEOUT (a bounded device wait ran out). */
+int cetra_batch_run(cetra_ctx *ctx, cetra_batch *batch, cetra_best *best);
+int cetra_batch_get_info(const cetra_batch *batch, cetra_batch_info *info);
+void cetra_batch_destroy(cetra_batch *batch);
+
+/* One-shot batched search: cetra_batch_create (no autotuning) + cetra_batch_run +
+ * cetra_batch_destroy. */
+int cetra_search_batch(cetra_ctx *ctx, const cetra_params *params, int n_curves,
+                       const int64_t *offsets, const double *time, const float *flux,
+                       const float *flux_err, const double *durations, int n_dur,
+                       const float *tmpl, int tmpl_len, const double *period_min,
+                       const double *period_max, const double *period_ratio, cetra_best *best);
+
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);
 

@@ -79,6 +79,9 @@ def _load():
     lib.oracle_periodic_at.argtypes = [ctypes.POINTER(_Geom), ctypes.c_int, P, P, P, P,
                                        ctypes.c_int, P, P, P, P, P]
     lib.oracle_logl0.argtypes = [ctypes.POINTER(_Geom), P, P]
+    lib.oracle_period_grid.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int64, P]
+    lib.oracle_period_grid.restype = ctypes.c_int64
     lib.oracle_logl0.restype = ctypes.c_double
     lib.oracle_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -216,6 +219,17 @@ def periodic(geom: Geometry, durations, depth, depth_var, lr, periods, mask=None
                                _ptr(out["duration"]), _ptr(out["depth"]),
                                _ptr(out["depth_var"]), _ptr(out["i"]), _ptr(out["j"])),
            "periodic")
+    return out
+
+
+def period_grid(pmin, ratio, pmax):
+    """The batched search's period grid: pmin * ratio^k (square-and-multiply) up to pmax."""
+    lib = _load()
+    n = lib.oracle_period_grid(float(pmin), float(ratio), float(pmax), 0, None)
+    if n < 0:
+        raise ValueError("bad period grid")
+    out = np.empty(n, np.float64)
+    lib.oracle_period_grid(float(pmin), float(ratio), float(pmax), n, _ptr(out))
     return out
 
 

@@ -441,6 +441,29 @@ int oracle_periodic_at(const oracle_geom *g, int n_dur, const double *depth,
 }
 
 /*
+ * Period grid of a batched search: P_k = pmin * ratio^k for k = 0, 1, ... while
+ * P_k <= pmax, with ratio^k by least-significant-bit-first square-and-multiply in
+ * FP64 (x = 1, b = ratio; for each bit of k: if set, x = x * b; then b = b * b).
+ * Writes at most `cap` periods and returns how many the grid has (or -1 on bad input).
+ */
+int64_t oracle_period_grid(double pmin, double ratio, double pmax, int64_t cap, double *out) {
+    if (!(pmin > 0.0) || !(ratio > 1.0) || !isfinite(pmax) || !isfinite(ratio)) return -1;
+    int64_t n = 0;
+    for (int64_t k = 0;; k++) {
+        double x = 1.0, b = ratio;
+        for (int64_t m = k; m; m >>= 1) {
+            if (m & 1) x = x * b;
+            b = b * b;
+        }
+        double P = pmin * x;
+        if (!(P <= pmax)) break;
+        if (n < cap) out[n] = P;
+        n++;
+    }
+    return n;
+}
+
+/*
  * Sec. 2.2 (last paragraph): the constant-flux log-likelihood, Eq. 1 at
  * Delta = 0 over the non-null grid points:
  *   logL0 = sum_{W_k > 0} [ -1/2 y_k^2 W_k - 1/2 ln(2 pi / W_k) ].

@@ -40,6 +40,23 @@ class cetra_plan_info(ctypes.Structure):
                 ("grid_bytes", ctypes.c_size_t)]
 
 
+class cetra_best(ctypes.Structure):
+    _fields_ = [("dlogl", ctypes.c_double), ("period", ctypes.c_double), ("t0", ctypes.c_double),
+                ("duration", ctypes.c_double), ("depth", ctypes.c_double),
+                ("depth_var", ctypes.c_double), ("k", ctypes.c_int64), ("i", ctypes.c_int64),
+                ("j", ctypes.c_int32), ("n_periods", ctypes.c_int32)]
+
+
+class cetra_batch_info(ctypes.Structure):
+    _fields_ = [("n_curves", ctypes.c_int32), ("n_dur", ctypes.c_int32),
+                ("n_points", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("n_t0", ctypes.c_int64), ("n_periods", ctypes.c_int64),
+                ("n_fold_items", ctypes.c_int64), ("fold_cell_reads", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("linear_threads", ctypes.c_int32),
+                ("fold_variant", ctypes.c_int32), ("fold_blocks", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
+
+
 class CetraError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -83,6 +100,13 @@ SIGNATURES = {
     "cetra_periodic_search": (_INT, [_P, _P, _P, _INT, _P, _P, _P, _P, _P, _P,
                                      ctypes.POINTER(_I64)]),
     "cetra_grid_free": (None, [_P]),
+    "cetra_batch_create": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
+                                  _INT, _P, _INT, _P, _P, _P, _INT, ctypes.POINTER(_P)]),
+    "cetra_batch_run": (_INT, [_P, _P, _P]),
+    "cetra_batch_get_info": (_INT, [_P, ctypes.POINTER(cetra_batch_info)]),
+    "cetra_batch_destroy": (None, [_P]),
+    "cetra_search_batch": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
+                                  _INT, _P, _INT, _P, _P, _P, _P]),
     "cetra_grid_get_info": (_INT, [_P, ctypes.POINTER(cetra_plan_info)]),
 }
 

@@ -269,3 +269,88 @@ def cetra_periodic_search(ctx: Context, grid: LinearGrid, periods, mask=None) ->
                                       ctypes.byref(best)), ctx.handle, "periodic_search")
     out["best_k"] = best.value
     return out
+
+
+# ----------------------------------------------------------------------------- batched form
+
+BEST_FIELDS = [f for f, _ in N.cetra_best._fields_]
+
+
+def _best_dict(arr):
+    return {f: np.array([getattr(b, f) for b in arr]) for f in BEST_FIELDS}
+
+
+def _pack(curves):
+    """CSR packing of a list of (time, flux, flux_err) arrays."""
+    lens = [len(c[0]) for c in curves]
+    off = np.zeros(len(curves) + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    t = np.ascontiguousarray(np.concatenate([np.asarray(c[0], np.float64) for c in curves]))
+    f = np.ascontiguousarray(np.concatenate([np.asarray(c[1], np.float32) for c in curves]))
+    e = np.ascontiguousarray(np.concatenate([np.asarray(c[2], np.float32) for c in curves]))
+    return off, t, f, e
+
+
+class Batch:
+    """cetra_batch_create / run / destroy over a list of (time, flux, flux_err) curves."""
+
+    def __init__(self, ctx: Context, curves, durations, tmpl, period_min, period_max=None,
+                 period_ratio=None, autotune=False, **params):
+        self.ctx = ctx
+        off, t, f, e = _pack(curves)
+        n = len(curves)
+        d = _np(durations, np.float64)
+        tm = _np(tmpl, np.float32)
+        pmin = _np(np.broadcast_to(period_min, (n,)), np.float64)
+        pmax = None if period_max is None else _np(np.broadcast_to(period_max, (n,)), np.float64)
+        rat = None if period_ratio is None else _np(np.broadcast_to(period_ratio, (n,)), np.float64)
+        self.params = make_params(**params)
+        self.handle = ctypes.c_void_p()
+        self._keep = (off, t, f, e, d, tm, pmin, pmax, rat)
+        check(N.lib.cetra_batch_create(ctx.handle, ctypes.byref(self.params), n, _ptr(off),
+                                       _ptr(t), _ptr(f), _ptr(e), _ptr(d), d.size, _ptr(tm),
+                                       tm.size, _ptr(pmin), _ptr(pmax), _ptr(rat),
+                                       int(bool(autotune)), ctypes.byref(self.handle)),
+              ctx.handle, "batch_create")
+        self.n = n
+
+    @property
+    def info(self) -> dict:
+        info = N.cetra_batch_info()
+        check(N.lib.cetra_batch_get_info(self.handle, ctypes.byref(info)), self.ctx.handle)
+        return {f: getattr(info, f) for f, _ in N.cetra_batch_info._fields_}
+
+    def run(self, results=True):
+        best = (N.cetra_best * self.n)() if results else None
+        check(N.lib.cetra_batch_run(self.ctx.handle, self.handle, best), self.ctx.handle,
+              "batch_run")
+        return _best_dict(best) if results else None
+
+    def close(self):
+        if self.handle:
+            N.lib.cetra_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cetra_search_batch(ctx: Context, curves, durations, tmpl, period_min, period_max=None,
+                       period_ratio=None, **params) -> dict:
+    """One-shot batched search (host buffers in, per-curve best model out)."""
+    off, t, f, e = _pack(curves)
+    n = len(curves)
+    d = _np(durations, np.float64)
+    tm = _np(tmpl, np.float32)
+    pmin = _np(np.broadcast_to(period_min, (n,)), np.float64)
+    pmax = None if period_max is None else _np(np.broadcast_to(period_max, (n,)), np.float64)
+    rat = None if period_ratio is None else _np(np.broadcast_to(period_ratio, (n,)), np.float64)
+    prm = make_params(**params)
+    best = (N.cetra_best * n)()
+    check(N.lib.cetra_search_batch(ctx.handle, ctypes.byref(prm), n, _ptr(off), _ptr(t), _ptr(f),
+                                   _ptr(e), _ptr(d), d.size, _ptr(tm), tm.size, _ptr(pmin),
+                                   _ptr(pmax), _ptr(rat), best), ctx.handle, "search_batch")
+    return _best_dict(best)

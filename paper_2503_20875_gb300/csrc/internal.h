@@ -95,6 +95,23 @@ constexpr uint32_t FT_SUSPEND_NS = 20000;            // suspend hint of one barr
 constexpr int FOLD_PAD = FT_STRIP + 16;  // zero cells after each grid row
 size_t fold_smem_bytes();
 
+// Device view of one light curve of a batch (cetra_batch_*).
+struct batch_curve {
+    double t_ref;         // smallest kept time
+    double pmin, ratio;   // period grid P_k = pmin * ratio^k (square-and-multiply), k < n_periods
+    int64_t pt_off;       // first input point
+    int64_t grid_off;     // first resampled cell
+    int64_t ab_off;       // first (A, B) cell
+    int64_t ld;           // (A, B) row stride (cells)
+    int32_t n_grid, I;    // resampled cells, t0 points (0: curve without usable points)
+    int32_t n_periods;
+    int32_t pad_;
+};
+
+// Period k of a batch curve: pmin * ratio^k with ratio^k by LSB-first square-and-multiply
+// in FP64 (one rounding per multiplication): the batch's period-grid definition.
+double batch_period_host(double pmin, double ratio, int64_t k);
+
 // Workspace layout (byte offsets, 256-aligned).
 struct ws_layout {
     size_t wy, w, ab, keys, logl0, status, total;
@@ -123,5 +140,26 @@ cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2
 cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
                          double *out);
 cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx);
+
+// Batched form (kernels.cu). `stream` is the batch's own stream (capturable).
+cudaError_t launch_batch_resample(cudaStream_t stream, int num_sms, const cetra_plan *plan,
+                                  const double *time, const float *flux, const float *err,
+                                  int64_t n_points, const int64_t *pt_offsets, int n_curves,
+                                  const batch_curve *curves, float *wy, float *w);
+cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int threads,
+                                const int64_t *tile_off, int n_curves, int64_t n_tiles,
+                                const batch_curve *curves, const float *wy, const float *w,
+                                float2 *ab);
+cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
+                              const float2 *ab, const batch_curve *curves,
+                              const int64_t *group_off, int n_curves, int64_t n_items,
+                              int *queue, unsigned long long *curve_keys, int *status);
+cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
+                                  const batch_curve *curves, int n_curves,
+                                  const unsigned long long *curve_keys, const int *status,
+                                  cetra_best *best);
+cudaError_t batch_configure(const cetra_plan *plan);
+int batch_fold_variants();
+int batch_fold_blocks_per_sm(int variant);
 
 int set_error(cetra_ctx *ctx, int code, const std::string &msg);

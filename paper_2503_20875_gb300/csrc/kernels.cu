@@ -122,8 +122,8 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
 // For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
 // KAHAN: every term is added with Kahan compensation (CETRA_FP32_KAHAN).
 template <int RB, bool KAHAN>
-__global__ void __launch_bounds__(128)
-linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
+__device__ __forceinline__ void linear_block(int tile, int jr, const float *__restrict__ wy,
+              const float *__restrict__ w, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
               const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
               int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
@@ -132,11 +132,10 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
     extern __shared__ float2 smem[];
     const int nthr = blockDim.x;
     const int t = threadIdx.x;
-    const int jr = blockIdx.y;
     const int j = jr / q, r = jr % q;
     const int64_t U = (r < I) ? (I - r + q - 1) / q : 0;
     const int64_t UT = (int64_t)nthr * RB;
-    const int64_t u0 = (int64_t)blockIdx.x * UT;
+    const int64_t u0 = (int64_t)tile * UT;
     if (u0 >= U) return;
     const int padlen = win_padlen[jr];
     const int64_t a0 = (int64_t)win_a[jr] + (int64_t)p * u0;
@@ -220,6 +219,17 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
         if (var) var[idx] = ok ? 1.0f / B : __int_as_float(0x7fc00000);
         if (dlogl) dlogl[idx] = ok ? 0.5f * (A * (A / B)) : __int_as_float(0x7fc00000);
     }
+}
+
+template <int RB, bool KAHAN>
+__global__ void __launch_bounds__(128)
+linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
+              const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
+              const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
+              int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
+              float *__restrict__ depth, float *__restrict__ var, float *__restrict__ dlogl) {
+    linear_block<RB, KAHAN>(blockIdx.x, blockIdx.y, wy, w, n_grid, tables, win_a, win_padlen,
+                            win_off, p, q, I, ld, kc_max, ab, depth, var, dlogl);
 }
 
 // Per-period key: larger LR wins; on equal LR the smaller flat index j*I + i wins
@@ -533,6 +543,125 @@ __device__ void fold_direct(fold_smem &sm, int g, int k, const float2 *__restric
     }
 }
 
+// Per-period metadata of slot t of a group (thread t < FT_G): P, Ps = P/s in t0 steps,
+// the number of phases and an upper bound on the epochs with o_e < I.
+__device__ __forceinline__ void fold_slot_meta(fold_smem &sm, int t, bool present, double P,
+                                               int I, double c, int64_t p, int64_t q) {
+    double Ps = 0.0;
+    int nph = 0, E = 0;
+    if (present) {
+        Ps = period_steps(P, c, p, q);
+        // a period shorter than one t0 step (or not finite) has no distinct phase: null
+        if (Ps >= 1.0 && isfinite(Ps)) {
+            const double cph = ceil(Ps);
+            nph = cph < (double)I ? (int)cph : I;
+            const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
+            E = eb < 2147483647.0 ? (int)eb : 2147483647;
+        }
+    } else {
+        P = 0.0;
+    }
+    sm.P[t] = P;
+    sm.Ps[t] = Ps;
+    sm.nph[t] = nph;
+    sm.E[t] = E;
+}
+
+// Fold the group whose slot metadata is in `sm` over one (A, B) grid: every sub-group
+// (8 -> 4 -> 2 -> 1 periods, as their offsets allow) in turn; the per-thread best key
+// of slot g ends in sm.best[g][t]. mask rows are (mask_k0 + g). Returns false if a
+// bulk copy timed out (uniform across the block).
+template <bool KAHAN, int R>
+__device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
+                           const float2 *__restrict__ ab, int I, int64_t ld, int J,
+                           const double *__restrict__ durations, const uint8_t *__restrict__ mask,
+                           int mask_k0, ring &iss, ring &con, int *__restrict__ status) {
+    const int t = threadIdx.x;
+    for (int g = 0; g < FT_G; ++g) sm.best[g][t] = 0ull;
+    __syncthreads();
+    for (int g0 = 0; g0 < FT_G;) {
+        // choose the sub-group [g0, g0 + Gs) and build its table:
+        // d [Es][Gs], tmin [Es], tlen [Es], full [Es]
+        int Gs = FT_G;
+        while (g0 % Gs) Gs >>= 1;
+        int Es = 0;
+        bool table_ok = false;
+        for (;;) {
+            Es = 0;
+            for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, sm.E[g]);
+            if ((int64_t)Es * (Gs + 3) > FT_TABLE) {
+                if (Gs > 1) {
+                    Gs >>= 1;
+                    continue;
+                }
+                break;  // a single period with too many epochs: no table
+            }
+            __syncthreads();
+            if (t == 0) sm.bad = 0;
+            int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es, *full = tlen + Es;
+            bool bad = false;
+            for (int e = t; e < Es; e += blockDim.x) {
+                int32_t o[FT_G];
+                int32_t mn = FT_SENT, mx = -1, nvalid = 0;
+                for (int gg = 0; gg < Gs; ++gg) {
+                    const int g = g0 + gg;
+                    o[gg] = FT_SENT;
+                    if (e < sm.E[g]) {
+                        const int64_t v = epoch_offset(e, sm.Ps[g]);
+                        if (v < I) o[gg] = (int32_t)v;
+                    }
+                    if (o[gg] != FT_SENT) {
+                        mn = min(mn, o[gg]);
+                        mx = max(mx, o[gg]);
+                        ++nvalid;
+                    }
+                }
+                for (int gg = 0; gg < Gs; ++gg)
+                    tab[e * Gs + gg] = o[gg] == FT_SENT ? FT_SENT : o[gg] - mn;
+                tmin[e] = mn;
+                tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
+                full[e] = nvalid == Gs;
+                if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
+            }
+            if (bad) sm.bad = 1;
+            __syncthreads();
+            if (sm.bad && Gs > 1) {
+                Gs >>= 1;
+                continue;
+            }
+            table_ok = !sm.bad;
+            break;
+        }
+        bool ok = true;
+        if (!table_ok) {
+            fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, durations, mask);
+        } else if (Gs == 8) {
+            ok = fold_subgroup<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
+                                            durations, mask, iss, con, status);
+        } else if (Gs == 4) {
+            ok = fold_subgroup<4, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
+                                            durations, mask, iss, con, status);
+        } else if (Gs == 2) {
+            ok = fold_subgroup<2, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
+                                            durations, mask, iss, con, status);
+        } else {
+            ok = fold_subgroup<1, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
+                                            durations, mask, iss, con, status);
+        }
+        if (!ok) return false;
+        g0 += Gs;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
 template <bool KAHAN>
 __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
 fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
@@ -543,114 +672,17 @@ fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     float2 *strips = reinterpret_cast<float2 *>(smem_raw);                      // [NSTAGE][STRIP]
     int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);  // FT_TABLE
     __shared__ fold_smem sm;
-
     const int t = threadIdx.x;
-    if (t == 0) {
-        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
+    fold_init_barriers(sm);
     ring iss, con;
-
     const int ngroups = (K + FT_G - 1) / FT_G;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int k0 = grp * FT_G;
         __syncthreads();  // the previous group is done with the shared tables
-        if (t < FT_G) {
-            const int k = k0 + t;
-            double P = 0.0, Ps = 0.0;
-            int nph = 0, E = 0;
-            if (k < K) {
-                P = periods[k];
-                Ps = period_steps(P, c, p, q);
-                // a period shorter than one t0 step (or not finite) has no distinct phase: null
-                if (Ps >= 1.0 && isfinite(Ps)) {
-                    const double cph = ceil(Ps);
-                    nph = cph < (double)I ? (int)cph : I;
-                    const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
-                    E = eb < 2147483647.0 ? (int)eb : 2147483647;
-                }
-            }
-            sm.P[t] = P;
-            sm.Ps[t] = Ps;
-            sm.nph[t] = nph;
-            sm.E[t] = E;
-        }
-        for (int g = 0; g < FT_G; ++g) sm.best[g][t] = 0ull;
-        __syncthreads();
-
-        for (int g0 = 0; g0 < FT_G;) {
-            // choose the sub-group [g0, g0 + Gs) and build its table:
-            // d [Es][Gs], tmin [Es], tlen [Es], full [Es]
-            int Gs = FT_G;
-            while (g0 % Gs) Gs >>= 1;
-            int Es = 0;
-            bool table_ok = false;
-            for (;;) {
-                Es = 0;
-                for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, sm.E[g]);
-                if ((int64_t)Es * (Gs + 3) > FT_TABLE) {
-                    if (Gs > 1) {
-                        Gs >>= 1;
-                        continue;
-                    }
-                    break;  // a single period with too many epochs: no table
-                }
-                __syncthreads();
-                if (t == 0) sm.bad = 0;
-                int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es, *full = tlen + Es;
-                bool bad = false;
-                for (int e = t; e < Es; e += blockDim.x) {
-                    int32_t o[FT_G];
-                    int32_t mn = FT_SENT, mx = -1, nvalid = 0;
-                    for (int gg = 0; gg < Gs; ++gg) {
-                        const int g = g0 + gg;
-                        o[gg] = FT_SENT;
-                        if (e < sm.E[g]) {
-                            const int64_t v = epoch_offset(e, sm.Ps[g]);
-                            if (v < I) o[gg] = (int32_t)v;
-                        }
-                        if (o[gg] != FT_SENT) {
-                            mn = min(mn, o[gg]);
-                            mx = max(mx, o[gg]);
-                            ++nvalid;
-                        }
-                    }
-                    for (int gg = 0; gg < Gs; ++gg)
-                        tab[e * Gs + gg] = o[gg] == FT_SENT ? FT_SENT : o[gg] - mn;
-                    tmin[e] = mn;
-                    tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
-                    full[e] = nvalid == Gs;
-                    if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
-                }
-                if (bad) sm.bad = 1;
-                __syncthreads();
-                if (sm.bad && Gs > 1) {
-                    Gs >>= 1;
-                    continue;
-                }
-                table_ok = !sm.bad;
-                break;
-            }
-            bool ok = true;
-            if (!table_ok) {
-                fold_direct(sm, g0, k0 + g0, ab, I, ld, J, durations, mask);
-            } else if (Gs == 8) {
-                ok = fold_subgroup<8, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
-                                      iss, con, status);
-            } else if (Gs == 4) {
-                ok = fold_subgroup<4, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
-                                      iss, con, status);
-            } else if (Gs == 2) {
-                ok = fold_subgroup<2, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
-                                      iss, con, status);
-            } else {
-                ok = fold_subgroup<1, KAHAN ? FT_R / 4 : FT_R, KAHAN>(sm, strips, tab, Es, g0, k0, ab, I, ld, J, durations, mask,
-                                      iss, con, status);
-            }
-            if (!ok) return;  // uniform: every thread saw the same vote
-            g0 += Gs;
-        }
+        if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
+        if (!fold_group<KAHAN, KAHAN ? FT_R / 4 : FT_R>(sm, strips, tab, ab, I, ld, J, durations,
+                                                         mask, k0, iss, con, status))
+            return;  // uniform: every thread saw the same vote
         for (int g = 0; g < FT_G; ++g) {
             const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
             if (t == 0 && k0 + g < K) keys[k0 + g] = v;
@@ -729,6 +761,202 @@ __global__ void logl0_kernel(const float *__restrict__ wy, const float *__restri
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) atomicAdd(out, acc);
     }
+}
+
+// ============================================================================================
+// Batched form: many light curves in one launch per stage.
+
+// Index of the curve owning item x of a CSR prefix array off[0..n] (off[c] <= x < off[c+1]).
+__device__ __forceinline__ int csr_find(const int64_t *__restrict__ off, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Period k of a batch curve: pmin * ratio^k, ratio^k by LSB-first square-and-multiply.
+__device__ __forceinline__ double batch_period(double pmin, double ratio, int64_t k) {
+    double x = 1.0, b = ratio;
+    while (k) {
+        if (k & 1) x = __dmul_rn(x, b);
+        b = __dmul_rn(b, b);
+        k >>= 1;
+    }
+    return __dmul_rn(pmin, x);
+}
+
+// Sec. 2.1.1 for every point of every curve (curve found from the point index).
+__global__ void batch_resample_kernel(const double *__restrict__ time,
+                                      const float *__restrict__ flux,
+                                      const float *__restrict__ err, int64_t n,
+                                      const int64_t *__restrict__ pt_off, int n_curves,
+                                      const batch_curve *__restrict__ curves, double c,
+                                      int64_t n_pad, int flux_is_offset, float *__restrict__ wy,
+                                      float *__restrict__ w) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const double tk = time[k];
+        const float fk = flux[k], ek = err[k];
+        if (!(isfinite(tk) && isfinite(fk) && isfinite(ek) && ek > 0.0f)) continue;
+        const batch_curve cv = curves[csr_find(pt_off, n_curves, k)];
+        const double v = floor(__dadd_rn(__ddiv_rn(__dsub_rn(tk, cv.t_ref), c), 0.5));
+        if (!(v >= -(double)n_pad) || !(v < (double)((int64_t)cv.n_grid - n_pad))) continue;
+        const int64_t bin = cv.grid_off + n_pad + (int64_t)v;
+        const float wk = 1.0f / (ek * ek);
+        const float yk = flux_is_offset ? fk : 1.0f - fk;
+        atomicAdd(&wy[bin], wk * yk);
+        atomicAdd(&w[bin], wk);
+    }
+}
+
+// Sec. 2.2 for every curve: x-blocks enumerate the t0 tiles of all curves.
+template <int RB, bool KAHAN>
+__global__ void __launch_bounds__(128)
+batch_linear_kernel(const int64_t *__restrict__ tile_off, int n_curves,
+                    const batch_curve *__restrict__ curves, const float *__restrict__ wy,
+                    const float *__restrict__ w, const float2 *__restrict__ tables,
+                    const int32_t *__restrict__ win_a, const int32_t *__restrict__ win_padlen,
+                    const int64_t *__restrict__ win_off, int p, int q, int kc_max,
+                    float2 *__restrict__ ab) {
+    const int cidx = csr_find(tile_off, n_curves, blockIdx.x);
+    const batch_curve cv = curves[cidx];
+    if (cv.I <= 0) return;
+    linear_block<RB, KAHAN>((int)(blockIdx.x - tile_off[cidx]), blockIdx.y, wy + cv.grid_off,
+                            w + cv.grid_off, cv.n_grid, tables, win_a, win_padlen, win_off, p, q,
+                            cv.I, cv.ld, kc_max, ab + cv.ab_off, nullptr, nullptr, nullptr);
+}
+
+// Sec. 2.3 for every curve: persistent blocks drain a queue of (curve, group of FT_G
+// periods) items; each group's best per period goes into the curve's key
+// (LR bits, inverted period index: the largest LR wins, ties to the smallest period index).
+template <bool KAHAN, int R>
+__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
+batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
+                  const int64_t *__restrict__ group_off, int n_curves, int64_t n_items, int J,
+                  const double *__restrict__ durations, double c, int64_t p, int64_t q,
+                  int *__restrict__ queue, unsigned long long *__restrict__ curve_keys,
+                  int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *strips = reinterpret_cast<float2 *>(smem_raw);
+    int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);
+    __shared__ fold_smem sm;
+    __shared__ int s_item;
+    const int t = threadIdx.x;
+    fold_init_barriers(sm);
+    ring iss, con;
+    for (;;) {
+        __syncthreads();  // the previous item is done with the shared state
+        if (t == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= n_items) break;
+        const int cidx = csr_find(group_off, n_curves, item);
+        const batch_curve cv = curves[cidx];
+        const int k0 = (int)(item - group_off[cidx]) * FT_G;
+        if (t < FT_G) {
+            const bool present = k0 + t < cv.n_periods;
+            fold_slot_meta(sm, t, present, present ? batch_period(cv.pmin, cv.ratio, k0 + t) : 0.0,
+                           cv.I, c, p, q);
+        }
+        if (!fold_group<KAHAN, R>(sm, strips, tab, ab + cv.ab_off, cv.I, cv.ld, J, durations,
+                                  nullptr, 0, iss, con, status))
+            return;  // uniform
+        for (int g = 0; g < FT_G; ++g) {
+            const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
+            if (t == 0 && v != 0ull && k0 + g < cv.n_periods)
+                atomicMax(&curve_keys[cidx], (v & 0xFFFFFFFF00000000ull) |
+                                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(k0 + g)));
+        }
+    }
+}
+
+// The winner of every curve: re-fold its best period over all (duration, phase) in the
+// fold's FP32 order to recover (j, i), then re-sum that window set in FP64.
+template <bool KAHAN>
+__global__ void __launch_bounds__(FOLD_THREADS)
+batch_finalize_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
+                      int n_curves, int J, const double *__restrict__ durations, double c,
+                      int64_t p, int64_t q, int64_t n_pad,
+                      const unsigned long long *__restrict__ curve_keys,
+                      const int *__restrict__ status, cetra_best *__restrict__ best) {
+    __shared__ unsigned long long red[FOLD_THREADS / 32];
+    const int cidx = blockIdx.x;
+    if (cidx >= n_curves) return;
+    const int t = threadIdx.x;
+    const batch_curve cv = curves[cidx];
+    const unsigned long long key = curve_keys[cidx];
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    cetra_best out;
+    out.dlogl = out.period = out.t0 = out.duration = out.depth = out.depth_var = nan;
+    out.k = out.i = -1;
+    out.j = -1;
+    out.n_periods = cv.n_periods;
+    if (key == 0ull || *status != 0) {
+        if (t == 0) best[cidx] = out;
+        return;
+    }
+    const int64_t k = (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+    const double P = batch_period(cv.pmin, cv.ratio, k);
+    const double Ps = period_steps(P, c, p, q);
+    const double cph = ceil(Ps);
+    const int nph = cph < (double)cv.I ? (int)cph : cv.I;
+    const float2 *grid = ab + cv.ab_off;
+    unsigned long long mine = 0ull;
+    for (int j = 0; j < J; ++j) {
+        if (!(durations[j] < P)) continue;
+        const float2 *row = grid + (int64_t)j * cv.ld;
+        for (int i = t; i < nph; i += blockDim.x) {
+            float2 s = make_float2(0.f, 0.f), nc = make_float2(0.f, 0.f);
+            for (int64_t e = 0;; ++e) {
+                const int64_t cell = i + epoch_offset(e, Ps);
+                if (cell >= cv.I) break;
+                if constexpr (KAHAN)
+                    kahan_add2(s, nc, row[cell]);
+                else
+                    add2(s, row[cell]);
+            }
+            if constexpr (KAHAN) add2(s, nc);
+            if (s.y > 0.0f) {
+                const float lr = 0.5f * (s.x * __fdividef(s.x, s.y));
+                const unsigned long long kk =
+                    make_key(lr, (uint32_t)j * (uint32_t)cv.I + (uint32_t)i);
+                mine = kk > mine ? kk : mine;
+            }
+        }
+    }
+    const unsigned long long win = block_max_key(mine, red);
+    if (t != 0) return;
+    if (win == 0ull) {
+        best[cidx] = out;
+        return;
+    }
+    const uint32_t flat = 0xFFFFFFFFu - (uint32_t)(win & 0xFFFFFFFFull);
+    const int j = (int)(flat / (uint32_t)cv.I), i = (int)(flat % (uint32_t)cv.I);
+    const float2 *row = grid + (int64_t)j * cv.ld;
+    double SA = 0.0, SB = 0.0;
+    for (int64_t e = 0;; ++e) {
+        const int64_t cell = i + epoch_offset(e, Ps);
+        if (cell >= cv.I) break;
+        SA = __dadd_rn(SA, (double)row[cell].x);
+        SB = __dadd_rn(SB, (double)row[cell].y);
+    }
+    const double Z = __ddiv_rn(SA, SB);
+    out.dlogl = 0.5 * __dmul_rn(SA, Z);
+    out.period = P;
+    out.t0 = __dadd_rn(cv.t_ref, __ddiv_rn(__dmul_rn((double)((int64_t)i * p - n_pad * q), c),
+                                          (double)q));
+    out.duration = durations[j];
+    out.depth = Z;
+    out.depth_var = __ddiv_rn(1.0, SB);
+    out.k = k;
+    out.i = i;
+    out.j = j;
+    best[cidx] = out;
 }
 
 }  // namespace
@@ -848,4 +1076,96 @@ cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy
     prof_mark(ctx, KID_LOGL0, false);
     ctx->launches++;
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------- batched
+
+double batch_period_host(double pmin, double ratio, int64_t k) {
+    double x = 1.0, b = ratio;
+    while (k) {
+        if (k & 1) x = x * b;
+        b = b * b;
+        k >>= 1;
+    }
+    return pmin * x;
+}
+
+cudaError_t launch_batch_resample(cudaStream_t stream, int num_sms, const cetra_plan *plan,
+                                  const double *time, const float *flux, const float *err,
+                                  int64_t n_points, const int64_t *pt_offsets, int n_curves,
+                                  const batch_curve *curves, float *wy, float *w) {
+    if (n_points <= 0) return cudaSuccess;
+    const int threads = 256;
+    int64_t blocks = (n_points + threads - 1) / threads;
+    if (blocks > (int64_t)num_sms * 32) blocks = (int64_t)num_sms * 32;
+    batch_resample_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
+        time, flux, err, n_points, pt_offsets, n_curves, curves, plan->cadence, plan->n_pad,
+        plan->flux_is_offset, wy, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int threads,
+                                const int64_t *tile_off, int n_curves, int64_t n_tiles,
+                                const batch_curve *curves, const float *wy, const float *w,
+                                float2 *ab) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (n_tiles > 2147483647) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)n_tiles, (unsigned)(plan->J * plan->q));
+    const size_t smem = ((size_t)plan->p * threads * LIN_RB + 2 * (size_t)plan->lin_kc) *
+                        sizeof(float2);
+    auto kern = plan->precision == CETRA_FP32_KAHAN ? batch_linear_kernel<LIN_RB, true>
+                                                    : batch_linear_kernel<LIN_RB, false>;
+    kern<<<grid, threads, smem, stream>>>(tile_off, n_curves, curves, wy, w, plan->d_tables,
+                                          plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
+                                          (int)plan->p, (int)plan->q, plan->lin_kc, ab);
+    return cudaGetLastError();
+}
+
+// Fold variants the autotuner chooses from: phases per thread (FT_R or FT_R / 2).
+int batch_fold_variants() { return 2; }
+int batch_fold_blocks_per_sm(int) { return FT_MIN_BLOCKS; }
+
+cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
+                              const float2 *ab, const batch_curve *curves,
+                              const int64_t *group_off, int n_curves, int64_t n_items,
+                              int *queue, unsigned long long *curve_keys, int *status) {
+    if (n_items <= 0) return cudaSuccess;
+    auto kern = batch_fold_kernel<false, FT_R>;
+    if (plan->precision == CETRA_FP32_KAHAN)
+        kern = batch_fold_kernel<true, FT_R / 4>;
+    else if (variant == 1)
+        kern = batch_fold_kernel<false, FT_R / 2>;
+    kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
+        ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
+        plan->p, plan->q, queue, curve_keys, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
+                                  const batch_curve *curves, int n_curves,
+                                  const unsigned long long *curve_keys, const int *status,
+                                  cetra_best *best) {
+    if (n_curves <= 0) return cudaSuccess;
+    auto kern = plan->precision == CETRA_FP32_KAHAN ? batch_finalize_kernel<true>
+                                                    : batch_finalize_kernel<false>;
+    kern<<<n_curves, FOLD_THREADS, 0, stream>>>(ab, curves, n_curves, plan->J, plan->d_durations,
+                                                plan->cadence, plan->p, plan->q, plan->n_pad,
+                                                curve_keys, status, best);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_configure(const cetra_plan *plan) {
+    const size_t lin_max = ((size_t)plan->p * 128 * LIN_RB + 2 * (size_t)plan->lin_kc) * sizeof(float2);
+    for (auto fn : {batch_linear_kernel<LIN_RB, false>, batch_linear_kernel<LIN_RB, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)lin_max);
+        if (e != cudaSuccess) return e;
+    }
+    for (auto fn : {batch_fold_kernel<false, FT_R>, batch_fold_kernel<false, FT_R / 2>,
+                    batch_fold_kernel<true, FT_R / 4>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fold_smem_bytes());
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }

@@ -530,3 +530,19 @@ def test_cell_evaluators_agree_with_full_search():
     lr, z, zv = oracle.periodic_at(g, r["depth"], r["depth_var"], r["dlogl"], P, per["i"], per["j"])
     np.testing.assert_array_equal(lr, per["dlogl"])
     np.testing.assert_array_equal(z, per["depth"])
+
+
+def test_batch_period_grid():
+    """The batched search's grid P_k = pmin ratio^k: matches the closed form within
+    the rounding of square-and-multiply (each squaring doubles the relative error of
+    the running power: at most about (k + 2 log2 k + 2) u), is increasing, and stops
+    at the last period <= pmax."""
+    u = 2.0 ** -53
+    for pmin, ratio, pmax in ((0.5, 1.0 + 1 / 48 / 340, 180.0), (1.0, 1.002, 42.5), (3.0, 2.0, 3.0)):
+        P = oracle.period_grid(pmin, ratio, pmax)
+        k = np.arange(P.size)
+        exact = pmin * ratio ** k
+        bound = (k + 2 * np.log2(k + 1) + 4) * u * exact
+        assert np.all(np.abs(P - exact) <= bound)
+        assert np.all(np.diff(P) > 0) and P[-1] <= pmax
+        assert pmin * ratio ** P.size > pmax * (1 - 1e-12)
