@@ -37,7 +37,7 @@ struct cetra_batch {
     float2 *d_ab = nullptr;
     int64_t *d_pt_off = nullptr, *d_tile_off = nullptr, *d_group_off = nullptr;
     batch_curve *d_curves = nullptr;
-    unsigned long long *d_keys = nullptr;
+    unsigned long long *d_keys = nullptr, *d_pkeys = nullptr;
     cetra_best *d_best = nullptr;
     int *d_queue = nullptr, *d_status = nullptr;
 };
@@ -116,11 +116,11 @@ cudaError_t enqueue(cetra_batch *b, int64_t n_items, int fold_variant, int lin_t
                                  b->d_curves, b->d_wy, b->d_w, b->d_ab)))
         return e;
     if ((e = launch_batch_fold(st, b->fold_blocks, fold_variant, plan, b->d_ab, b->d_curves,
-                               b->d_group_off, b->n_curves, n_items, b->d_queue, b->d_keys,
-                               b->d_status)))
+                               b->d_group_off, b->n_curves, n_items, b->d_queue, b->d_pkeys,
+                               b->d_keys, b->d_status)))
         return e;
-    return launch_batch_finalize(st, plan, b->d_ab, b->d_curves, b->n_curves, b->d_keys,
-                                 b->d_status, b->d_best);
+    return launch_batch_finalize(st, plan, b->d_ab, b->d_curves, b->n_curves, b->d_pkeys,
+                                 b->d_keys, b->d_status, b->d_best);
 }
 
 // Milliseconds of one enqueue() with the given shapes (the batch is rebuilt by the caller).
@@ -279,6 +279,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
         }
         cv.grid_off = grid;
         cv.ab_off = abc;
+        cv.per_off = per;
         grid += cv.n_grid;
         abc += (int64_t)n_dur * cv.ld;
         t0s += cv.I;
@@ -296,7 +297,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     // device memory, one allocation carved in 256-byte aligned pieces
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0, o_time, o_flux, o_err, o_wy, o_w, o_ab, o_pt, o_tile, o_grp, o_cv, o_keys,
-                    o_best, o_q;
+                    o_pkeys, o_best, o_q;
     o_time = off; off = up(off + (size_t)n_points * sizeof(double));
     o_flux = off; off = up(off + (size_t)n_points * sizeof(float));
     o_err = off; off = up(off + (size_t)n_points * sizeof(float));
@@ -308,6 +309,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_grp = off; off = up(off + (size_t)(n_curves + 1) * sizeof(int64_t));
     o_cv = off; off = up(off + (size_t)n_curves * sizeof(batch_curve));
     o_keys = off; off = up(off + (size_t)n_curves * sizeof(unsigned long long));
+    o_pkeys = off; off = up(off + (size_t)std::max<int64_t>(per, 1) * sizeof(unsigned long long));
     o_best = off; off = up(off + (size_t)n_curves * sizeof(cetra_best));
     o_q = off; off = up(off + 2 * sizeof(int));
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -330,6 +332,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     b->d_group_off = reinterpret_cast<int64_t *>(base + o_grp);
     b->d_curves = reinterpret_cast<batch_curve *>(base + o_cv);
     b->d_keys = reinterpret_cast<unsigned long long *>(base + o_keys);
+    b->d_pkeys = reinterpret_cast<unsigned long long *>(base + o_pkeys);
     b->d_best = reinterpret_cast<cetra_best *>(base + o_best);
     b->d_queue = reinterpret_cast<int *>(base + o_q);
     b->d_status = b->d_queue + 1;

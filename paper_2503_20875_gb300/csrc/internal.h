@@ -103,6 +103,7 @@ struct batch_curve {
     int64_t grid_off;     // first resampled cell
     int64_t ab_off;       // first (A, B) cell
     int64_t ld;           // (A, B) row stride (cells)
+    int64_t per_off;      // first period (index into the batch's per-period keys)
     int32_t n_grid, I;    // resampled cells, t0 points (0: curve without usable points)
     int32_t n_periods;
     int32_t pad_;
@@ -153,9 +154,11 @@ cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int
 cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
                               const float2 *ab, const batch_curve *curves,
                               const int64_t *group_off, int n_curves, int64_t n_items,
-                              int *queue, unsigned long long *curve_keys, int *status);
+                              int *queue, unsigned long long *period_keys,
+                              unsigned long long *curve_keys, int *status);
 cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
                                   const batch_curve *curves, int n_curves,
+                                  const unsigned long long *period_keys,
                                   const unsigned long long *curve_keys, const int *status,
                                   cetra_best *best);
 cudaError_t batch_configure(const cetra_plan *plan);

@@ -337,6 +337,7 @@ struct fold_smem {
     int nph[FT_G];
     int E[FT_G];
     int bad;
+    int tight;  // some epoch's spread leaves less than the sliced path's margin
 };
 
 // Ring of bulk copies: `n` counts copies issued (thread 0) or consumed (all threads);
@@ -517,6 +518,141 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
     return true;
 }
 
+// A sub-group whose periods all have few phases (nph <= Tp <= T/2, Tp a power of two):
+// the lanes L = t + FT_THREADS r of the block form H = T / Tp epoch slices of Tp phases;
+// slice h folds epochs e = s H + h of super-epoch s, and one bulk copy per super-epoch
+// covers its H epochs. The H partial sums of every phase are then added in slice order
+// through shared memory. (Strip bound: tmin grows by at most Tp + 1 per epoch, so a
+// super-epoch needs at most T + spread + 3 cells; the table check keeps spread <=
+// FT_STRIP - FT_T - 8 for this path.)
+template <int GS, int R, bool KAHAN>
+__device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_t *tab, int Es,
+                                     int g0, int mask_k0, const float2 *__restrict__ ab, int I,
+                                     int64_t ld, int J, const double *__restrict__ durations,
+                                     const uint8_t *__restrict__ mask, ring &iss, ring &con,
+                                     int *__restrict__ status, int tp_log2) {
+    constexpr int T = FT_THREADS * R;
+    const int Tp = 1 << tp_log2, H = T >> tp_log2;
+    const int t = threadIdx.x;
+    const int32_t *d = tab;
+    const int32_t *tmin = tab + Es * GS;
+    const int32_t *tlen = tmin + Es;
+    const int32_t *full = tlen + Es;
+    float best_lr[GS];
+    uint32_t best_at[GS];
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        best_lr[gg] = -1.0f;
+        best_at[gg] = 0u;
+    }
+    auto live_epoch = [&](int e) { return e < Es && tmin[e] < I; };
+    for (int j = 0; j < J; ++j) {
+        const double D = durations[j];
+        unsigned use = 0u;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            const int g = g0 + gg;
+            if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(mask_k0 + g) * J + j]))
+                use |= 1u << gg;
+        }
+        if (!use) continue;
+        const bool all_used = use == (1u << GS) - 1u;
+        const float2 *row = ab + (int64_t)j * ld;
+        float2 acc[GS][R];
+        float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+        if constexpr (KAHAN) {
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+        }
+        auto issue = [&](int sidx) {
+            const int e0 = sidx * H;
+            const int a = tmin[e0] & ~1;
+            int end = 0;
+            for (int h = 0; h < H; ++h)
+                if (live_epoch(e0 + h)) end = max(end, tmin[e0 + h] + tlen[e0 + h] + Tp);
+            const int len = ((end - a) + 1) & ~1;
+            const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
+            fence_proxy_async();
+            mbar_expect_tx(&sm.bar[iss.stage], bytes);
+            bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
+            iss.next();
+        };
+        if (t == 0)
+            for (int sidx = 0; sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx) issue(sidx);
+        for (int sidx = 0; live_epoch(sidx * H); ++sidx) {
+            if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H)) issue(sidx + FT_NSTAGE - 1);
+            const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
+            const float2 *S = strips + con.stage * FT_STRIP - (tmin[sidx * H] & ~1);
+            con.next();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int L = t + r * FT_THREADS;
+                const int e = sidx * H + (L >> tp_log2);
+                if (!live_epoch(e)) continue;
+                const float2 *src = S + (L & (Tp - 1)) + tmin[e];
+                const int32_t *de = d + e * GS;
+                const bool fast = all_used && full[e];
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg) {
+                    const int32_t dg = de[gg];
+                    if (!fast && (dg == FT_SENT || !((use >> gg) & 1u))) continue;
+                    if constexpr (KAHAN)
+                        kahan_add2(acc[gg][r], cmp[gg][r], src[dg]);
+                    else
+                        add2(acc[gg][r], src[dg]);
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                if (t == 0) {
+                    atomicExch(status, CETRA_ETIMEOUT);
+                    while (con.n < iss.n) {
+                        mbar_wait(&sm.bar[con.stage], con.parity);
+                        con.next();
+                    }
+                }
+                return false;
+            }
+        }
+        // every copy is consumed: the strip ring is free to hold one period's partial sums
+        float2 *part = strips;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            if (!((use >> gg) & 1u)) continue;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v = acc[gg][r];
+                if constexpr (KAHAN) add2(v, cmp[gg][r]);
+                part[t + r * FT_THREADS] = v;
+            }
+            __syncthreads();
+            const int nph = sm.nph[g0 + gg];
+            for (int phi = t; phi < Tp; phi += FT_THREADS) {
+                float2 v = part[phi];
+                for (int h = 1; h < H; ++h) add2(v, part[h * Tp + phi]);
+                const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
+                if (phi < nph && v.y > 0.0f && lr > best_lr[gg]) {
+                    best_lr[gg] = lr;
+                    best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)phi;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg)
+        if (best_lr[gg] >= 0.0f) {
+            const unsigned long long key = make_key(best_lr[gg], best_at[gg]);
+            if (key > sm.best[g0 + gg][t]) sm.best[g0 + gg][t] = key;
+        }
+    return true;
+}
+
 // One period whose offsets do not fit the table: straight from global memory.
 __device__ void fold_direct(fold_smem &sm, int g, int k, const float2 *__restrict__ ab, int I,
                             int64_t ld, int J, const double *__restrict__ durations,
@@ -597,9 +733,9 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
                 break;  // a single period with too many epochs: no table
             }
             __syncthreads();
-            if (t == 0) sm.bad = 0;
+            if (t == 0) sm.bad = sm.tight = 0;
             int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es, *full = tlen + Es;
-            bool bad = false;
+            bool bad = false, tight = false;
             for (int e = t; e < Es; e += blockDim.x) {
                 int32_t o[FT_G];
                 int32_t mn = FT_SENT, mx = -1, nvalid = 0;
@@ -622,8 +758,10 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
                 tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
                 full[e] = nvalid == Gs;
                 if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
+                if (mx - mn > FT_STRIP - FT_T - 8) tight = true;
             }
             if (bad) sm.bad = 1;
+            if (tight) sm.tight = 1;
             __syncthreads();
             if (sm.bad && Gs > 1) {
                 Gs >>= 1;
@@ -632,9 +770,33 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
             table_ok = !sm.bad;
             break;
         }
+        // periods with few phases: fold several epochs at once (epoch slices)
+        int nph_sub = 0;
+        for (int g = g0; g < g0 + Gs; ++g) nph_sub = max(nph_sub, sm.nph[g]);
+        int tp_log2 = 5;
+        while ((1 << tp_log2) < nph_sub) ++tp_log2;
+        const bool sliced = table_ok && !sm.tight && nph_sub > 0 &&
+                            (2 << tp_log2) <= FT_THREADS * R;
         bool ok = true;
         if (!table_ok) {
             fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, durations, mask);
+        } else if (sliced) {
+            if (Gs == 8)
+                ok = fold_subgroup_sliced<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
+                                                       ld, J, durations, mask, iss, con, status,
+                                                       tp_log2);
+            else if (Gs == 4)
+                ok = fold_subgroup_sliced<4, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
+                                                       ld, J, durations, mask, iss, con, status,
+                                                       tp_log2);
+            else if (Gs == 2)
+                ok = fold_subgroup_sliced<2, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
+                                                       ld, J, durations, mask, iss, con, status,
+                                                       tp_log2);
+            else
+                ok = fold_subgroup_sliced<1, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
+                                                       ld, J, durations, mask, iss, con, status,
+                                                       tp_log2);
         } else if (Gs == 8) {
             ok = fold_subgroup<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
                                             durations, mask, iss, con, status);
@@ -839,8 +1001,8 @@ __global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
 batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
                   const int64_t *__restrict__ group_off, int n_curves, int64_t n_items, int J,
                   const double *__restrict__ durations, double c, int64_t p, int64_t q,
-                  int *__restrict__ queue, unsigned long long *__restrict__ curve_keys,
-                  int *__restrict__ status) {
+                  int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
+                  unsigned long long *__restrict__ curve_keys, int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *strips = reinterpret_cast<float2 *>(smem_raw);
     int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);
@@ -868,26 +1030,29 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
             return;  // uniform
         for (int g = 0; g < FT_G; ++g) {
             const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
-            if (t == 0 && v != 0ull && k0 + g < cv.n_periods)
-                atomicMax(&curve_keys[cidx], (v & 0xFFFFFFFF00000000ull) |
-                                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(k0 + g)));
+            if (t == 0 && k0 + g < cv.n_periods) {
+                period_keys[cv.per_off + k0 + g] = v;
+                if (v != 0ull)
+                    atomicMax(&curve_keys[cidx],
+                              (v & 0xFFFFFFFF00000000ull) |
+                                  (unsigned long long)(0xFFFFFFFFu - (uint32_t)(k0 + g)));
+            }
         }
     }
 }
 
-// The winner of every curve: re-fold its best period over all (duration, phase) in the
-// fold's FP32 order to recover (j, i), then re-sum that window set in FP64.
-template <bool KAHAN>
-__global__ void __launch_bounds__(FOLD_THREADS)
-batch_finalize_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
-                      int n_curves, int J, const double *__restrict__ durations, double c,
-                      int64_t p, int64_t q, int64_t n_pad,
-                      const unsigned long long *__restrict__ curve_keys,
-                      const int *__restrict__ status, cetra_best *__restrict__ best) {
-    __shared__ unsigned long long red[FOLD_THREADS / 32];
-    const int cidx = blockIdx.x;
+// The winner of every curve: its best period from the curve key, that period's best
+// (duration, t0) from its own key, re-summed in FP64.
+__global__ void batch_finalize_kernel(const float2 *__restrict__ ab,
+                                      const batch_curve *__restrict__ curves, int n_curves,
+                                      const double *__restrict__ durations, double c, int64_t p,
+                                      int64_t q, int64_t n_pad,
+                                      const unsigned long long *__restrict__ period_keys,
+                                      const unsigned long long *__restrict__ curve_keys,
+                                      const int *__restrict__ status,
+                                      cetra_best *__restrict__ best) {
+    const int cidx = blockIdx.x * blockDim.x + threadIdx.x;
     if (cidx >= n_curves) return;
-    const int t = threadIdx.x;
     const batch_curve cv = curves[cidx];
     const unsigned long long key = curve_keys[cidx];
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
@@ -897,47 +1062,16 @@ batch_finalize_kernel(const float2 *__restrict__ ab, const batch_curve *__restri
     out.j = -1;
     out.n_periods = cv.n_periods;
     if (key == 0ull || *status != 0) {
-        if (t == 0) best[cidx] = out;
-        return;
-    }
-    const int64_t k = (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
-    const double P = batch_period(cv.pmin, cv.ratio, k);
-    const double Ps = period_steps(P, c, p, q);
-    const double cph = ceil(Ps);
-    const int nph = cph < (double)cv.I ? (int)cph : cv.I;
-    const float2 *grid = ab + cv.ab_off;
-    unsigned long long mine = 0ull;
-    for (int j = 0; j < J; ++j) {
-        if (!(durations[j] < P)) continue;
-        const float2 *row = grid + (int64_t)j * cv.ld;
-        for (int i = t; i < nph; i += blockDim.x) {
-            float2 s = make_float2(0.f, 0.f), nc = make_float2(0.f, 0.f);
-            for (int64_t e = 0;; ++e) {
-                const int64_t cell = i + epoch_offset(e, Ps);
-                if (cell >= cv.I) break;
-                if constexpr (KAHAN)
-                    kahan_add2(s, nc, row[cell]);
-                else
-                    add2(s, row[cell]);
-            }
-            if constexpr (KAHAN) add2(s, nc);
-            if (s.y > 0.0f) {
-                const float lr = 0.5f * (s.x * __fdividef(s.x, s.y));
-                const unsigned long long kk =
-                    make_key(lr, (uint32_t)j * (uint32_t)cv.I + (uint32_t)i);
-                mine = kk > mine ? kk : mine;
-            }
-        }
-    }
-    const unsigned long long win = block_max_key(mine, red);
-    if (t != 0) return;
-    if (win == 0ull) {
         best[cidx] = out;
         return;
     }
-    const uint32_t flat = 0xFFFFFFFFu - (uint32_t)(win & 0xFFFFFFFFull);
+    const int64_t k = (int64_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+    const unsigned long long pk = period_keys[cv.per_off + k];
+    const uint32_t flat = 0xFFFFFFFFu - (uint32_t)(pk & 0xFFFFFFFFull);
     const int j = (int)(flat / (uint32_t)cv.I), i = (int)(flat % (uint32_t)cv.I);
-    const float2 *row = grid + (int64_t)j * cv.ld;
+    const double P = batch_period(cv.pmin, cv.ratio, k);
+    const double Ps = period_steps(P, c, p, q);
+    const float2 *row = ab + cv.ab_off + (int64_t)j * cv.ld;
     double SA = 0.0, SB = 0.0;
     for (int64_t e = 0;; ++e) {
         const int64_t cell = i + epoch_offset(e, Ps);
@@ -1128,7 +1262,8 @@ int batch_fold_blocks_per_sm(int) { return FT_MIN_BLOCKS; }
 cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
                               const float2 *ab, const batch_curve *curves,
                               const int64_t *group_off, int n_curves, int64_t n_items,
-                              int *queue, unsigned long long *curve_keys, int *status) {
+                              int *queue, unsigned long long *period_keys,
+                              unsigned long long *curve_keys, int *status) {
     if (n_items <= 0) return cudaSuccess;
     auto kern = batch_fold_kernel<false, FT_R>;
     if (plan->precision == CETRA_FP32_KAHAN)
@@ -1137,20 +1272,20 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
         kern = batch_fold_kernel<false, FT_R / 2>;
     kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
         ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
-        plan->p, plan->q, queue, curve_keys, status);
+        plan->p, plan->q, queue, period_keys, curve_keys, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
                                   const batch_curve *curves, int n_curves,
+                                  const unsigned long long *period_keys,
                                   const unsigned long long *curve_keys, const int *status,
                                   cetra_best *best) {
     if (n_curves <= 0) return cudaSuccess;
-    auto kern = plan->precision == CETRA_FP32_KAHAN ? batch_finalize_kernel<true>
-                                                    : batch_finalize_kernel<false>;
-    kern<<<n_curves, FOLD_THREADS, 0, stream>>>(ab, curves, n_curves, plan->J, plan->d_durations,
-                                                plan->cadence, plan->p, plan->q, plan->n_pad,
-                                                curve_keys, status, best);
+    const int threads = 128;
+    batch_finalize_kernel<<<(n_curves + threads - 1) / threads, threads, 0, stream>>>(
+        ab, curves, n_curves, plan->d_durations, plan->cadence, plan->p, plan->q, plan->n_pad,
+        period_keys, curve_keys, status, best);
     return cudaGetLastError();
 }
 
