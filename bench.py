@@ -198,18 +198,10 @@ def run_reference(args):
 
 
 def batch_periods(pmin, ratio, pmax):
-    """The batched search's period grid, pmin * ratio^k (LSB-first square-and-multiply in
-    FP64, as cetra_batch_create defines it), k = 0.. while <= pmax."""
+    """The batched search's period grid up to pmax (cetra_batch_create's definition)."""
+    from paper_2503_20875_gb300.api import batch_period_grid
     n = int(np.floor(np.log(pmax / pmin) / np.log(ratio))) + 3
-    k = np.arange(n, dtype=np.int64)
-    x = np.ones(n)
-    b = np.full(n, ratio)
-    m = k.copy()
-    while np.any(m):
-        x = np.where(m & 1, x * b, x)
-        b = b * b
-        m >>= 1
-    P = pmin * x
+    P = batch_period_grid(pmin, ratio, n)
     return P[P <= pmax]
 
 

@@ -302,6 +302,9 @@ typedef struct {
     int32_t fold_variant;    /* chosen fold variant (phases per thread, blocks per SM) */
     int32_t fold_blocks;     /* persistent fold blocks */
     int32_t graph;           /* 1 once the run is captured as a CUDA graph */
+    double cadence;          /* shared resample cadence c (days) */
+    double t0_step;          /* shared realised t0 step s = c p / q (days) */
+    int64_t p, q, n_pad;     /* shared t0 ticks and null padding (see cetra_plan_info) */
 } cetra_batch_info;
 
 /*
@@ -327,6 +330,33 @@ int cetra_batch_run(cetra_ctx *ctx, cetra_batch *batch, cetra_best *best);
 int cetra_batch_get_info(const cetra_batch *batch, cetra_batch_info *info);
 void cetra_batch_destroy(cetra_batch *batch);
 
+/*
+ * Linear-search features of every curve (resample + linear search, Sec. 2.2): the window
+ * likelihood ratio A^2/(2B) of the windows with a positive depth (A > 0), max-pooled over
+ * n_bins equal bins of each curve's t0 grid (bin width ceil(n_t0 / n_bins)); empty bins,
+ * null windows and negative depths give 0. d_features: device FP32
+ * [n_curves][n_dur][n_bins], caller-owned. Blocks until done. (Input of the learned
+ * period-interval proposal, which is not in the paper.)
+ */
+int cetra_batch_features(cetra_ctx *ctx, cetra_batch *batch, int n_bins, float *d_features);
+
+/*
+ * Fold only the listed work items and report each curve's best over them. An item is one
+ * group of 8 consecutive periods of one curve: curve c's items are
+ * first_item(c) .. first_item(c) + ceil(n_periods(c) / 8) - 1 (cetra_batch_curve), item x
+ * covering periods 8 (x - first_item(c)) .. + 7. items: host int64 [n_items]. linear != 0
+ * reruns the resample and linear stages first (needed unless cetra_batch_features or a
+ * run has just left this batch's grids). best as in cetra_batch_run (a curve none of whose
+ * items is listed is null). Blocks until done.
+ */
+int cetra_batch_run_items(cetra_ctx *ctx, cetra_batch *batch, const int64_t *items,
+                          int64_t n_items, int linear, cetra_best *best);
+
+/* Geometry and period grid of curve `curve` of a batch (outputs may be NULL). */
+int cetra_batch_curve(const cetra_batch *batch, int curve, double *t_ref, double *period_min,
+                      double *period_ratio, int32_t *n_periods, int32_t *n_t0,
+                      int64_t *first_item);
+
 /* One-shot batched search: cetra_batch_create (no autotuning) + cetra_batch_run +
  * cetra_batch_destroy. */
 int cetra_search_batch(cetra_ctx *ctx, const cetra_params *params, int n_curves,
@@ -334,6 +364,52 @@ int cetra_search_batch(cetra_ctx *ctx, const cetra_params *params, int n_curves,
                        const float *flux_err, const double *durations, int n_dur,
                        const float *tmpl, int tmpl_len, const double *period_min,
                        const double *period_max, const double *period_ratio, cetra_best *best);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned period-interval proposal (not in the paper): a 1-D CNN over a curve's max-pooled
+ * linear-search likelihood ratios [n_dur][n_bins] (cetra_batch_features) that marks the bins
+ * holding transits, and a comb that turns that map into scores of log-spaced period
+ * intervals, so that the fold can evaluate the most promising intervals only. Network:
+ * log1p(x) -> conv(in -> 32, k 9) ReLU -> conv(32 -> 32) ReLU -> conv(32 -> 32) ReLU ->
+ * conv(32 -> 1), zero padding; FP32 training copy of the weights, BF16 weights in every
+ * kernel, FP32 sums. Parameters (flat FP32): for each layer W [out][in][9] then b [out].
+ * ------------------------------------------------------------------------------------- */
+typedef struct cetra_cnn cetra_cnn;
+
+/* in_channels 1..32 (the durations), n_bins a multiple of 256, He-normal initial weights
+ * from `seed`. Device buffers sized for max_batch curves. */
+int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch, uint64_t seed,
+                     cetra_cnn **cnn);
+void cetra_cnn_destroy(cetra_cnn *cnn);
+int64_t cetra_cnn_param_count(const cetra_cnn *cnn);
+int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *cnn, float *host_params);
+/* Replaces the parameters and resets the optimiser state. */
+int cetra_cnn_set_params(cetra_ctx *ctx, cetra_cnn *cnn, const float *host_params);
+/* d_features: device [B][in][n_bins]; d_prob: device [B][n_bins], sigmoid of the logits. */
+int cetra_cnn_forward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features, int B,
+                      float *d_prob);
+/* Forward + backward of the weighted binary cross-entropy with logits against d_labels
+ * (device [B][n_bins], 0 or 1), mean over bins, positive weight pos_weight. Leaves the
+ * gradient on the device for cetra_cnn_adam; *loss and host_grads (flat, like the
+ * parameters) are filled when not NULL (that synchronises). */
+int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features,
+                       const float *d_labels, int B, float pos_weight, double *loss,
+                       float *host_grads);
+/* One Adam step with the last gradient (bias-corrected), then re-rounds the BF16 weights. */
+int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *cnn, float lr, float beta1, float beta2,
+                   float eps);
+/* Comb scores of n_intervals log-spaced period intervals between p_lo and p_hi days for each
+ * of B per-bin maps d_prob [B][n_bins] (bin widths d_bin_days [B] days, device FP64): the
+ * best, over trial periods and phases, of sum_e p(t_e) / sqrt(E) with
+ * t_e = floor(phase + e P + 1/2) < n_bins. Interval q spans p_lo (p_hi/p_lo)^(q/n) ..
+ * p_lo (p_hi/p_lo)^((q+1)/n); its trials split it into max(1, ceil(width n_bins / lo)) equal
+ * parts (in bins) and take their midpoints, so the last epoch's phase moves by about one bin
+ * between neighbouring trials; trials below 1 bin or above n_bins are skipped, and a curve
+ * with bin width <= 0 scores 0. d_scores: device FP32 [B][n_intervals]. Asynchronous on the
+ * context's stream. Errors: CETRA_EINVAL (bad sizes, p_lo <= 0, p_hi <= p_lo). */
+int cetra_cnn_comb(cetra_ctx *ctx, const float *d_prob, int B, int n_bins,
+                   const double *d_bin_days, double p_lo, double p_hi, int n_intervals,
+                   float *d_scores);
 
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);

@@ -1,0 +1,171 @@
+"""FP64 reference of the period-interval proposal network (test infrastructure only).
+
+Plain definitions, no blocking or fusion, used to check the CUDA forward pass and
+gradients on small inputs:
+  x0 = log1p(max(features, 0))
+  conv(x; W, b)[o, t] = b[o] + sum_i sum_k W[o, i, k] x[i, t + k - 4]   (zero padding)
+  layers: conv(in -> 32) ReLU, conv(32 -> 32) ReLU, conv(32 -> 32) ReLU, conv(32 -> 1)
+  weights rounded to BF16 (nearest even) before use, biases FP32
+  loss = mean over bins of  w+ y softplus(-z) + (1 - y) softplus(z)
+Gradients are taken with respect to the rounded weights (what the kernels use).
+The flat parameter layout is, per layer, W [out][in][9] then b [out].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K = 9
+HALF = K // 2
+HIDDEN = 32
+LAYERS = 4
+
+
+def bf16_round(w):
+    """Round FP32 values to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(w, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u >> 16) & 1) + 0x7FFF
+    u = ((u + r) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def shapes(cin):
+    out = []
+    for l in range(LAYERS):
+        i = cin if l == 0 else HIDDEN
+        o = 1 if l == LAYERS - 1 else HIDDEN
+        out.append((o, i))
+    return out
+
+
+def unflatten(params, cin):
+    p = np.asarray(params, np.float32)
+    layers, off = [], 0
+    for o, i in shapes(cin):
+        W = bf16_round(p[off:off + o * i * K]).reshape(o, i, K)
+        off += o * i * K
+        b = p[off:off + o].astype(np.float64)
+        off += o
+        layers.append((W, b))
+    assert off == p.size
+    return layers
+
+
+def conv(x, W, b):
+    B, cin, T = x.shape
+    xp = np.zeros((B, cin, T + 2 * HALF))
+    xp[:, :, HALF:HALF + T] = x
+    y = np.zeros((B, W.shape[0], T)) + b[None, :, None]
+    for k in range(K):
+        y += np.einsum("oi,bit->bot", W[:, :, k], xp[:, :, k:k + T])
+    return y, xp
+
+
+def forward(params, features):
+    f = np.asarray(features, np.float64)
+    return forward_layers(unflatten(params, f.shape[1]), features)
+
+
+def forward_layers(layers, features):
+    f = np.asarray(features, np.float64)
+    x = np.log1p(np.maximum(f.astype(np.float32).astype(np.float64), 0.0))
+    acts = [x]
+    pads = []
+    for l, (W, b) in enumerate(layers):
+        y, xp = conv(acts[-1], W, b)
+        pads.append(xp)
+        if l < LAYERS - 1:
+            y = np.maximum(y, 0.0)
+        acts.append(y)
+    return acts, pads, layers
+
+
+def loss_and_grads(params, features, labels, pos_weight):
+    f = np.asarray(features, np.float64)
+    return loss_and_grads_layers(unflatten(params, f.shape[1]), features, labels, pos_weight)
+
+
+def loss_and_grads_layers(layers, features, labels, pos_weight):
+    acts, pads, layers = forward_layers(layers, features)
+    z = acts[-1][:, 0, :]
+    y = np.asarray(labels, np.float64)
+    n = z.size
+    sp = np.logaddexp(0.0, z)          # softplus(z)
+    loss = np.mean(pos_weight * y * (sp - z) + (1 - y) * sp)
+    s = 1.0 / (1.0 + np.exp(-z))
+    g = ((s * (pos_weight * y + 1 - y) - pos_weight * y) / n)[:, None, :]
+    grads = [None] * LAYERS
+    for l in range(LAYERS - 1, -1, -1):
+        W, b = layers[l]
+        if l < LAYERS - 1:
+            g = g * (acts[l + 1] > 0)
+        xp = pads[l]
+        T = g.shape[2]
+        dW = np.zeros_like(W)
+        for k in range(K):
+            dW[:, :, k] = np.einsum("bot,bit->oi", g, xp[:, :, k:k + T])
+        db = g.sum(axis=(0, 2))
+        grads[l] = (dW, db)
+        if l > 0:
+            dxp = np.zeros_like(xp)
+            for k in range(K):
+                dxp[:, :, k:k + T] += np.einsum("oi,bot->bit", W[:, :, k], g)
+            g = dxp[:, :, HALF:HALF + T]
+    flat = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
+    return loss, flat
+
+
+def probabilities(params, features):
+    acts, _, _ = forward(params, features)
+    return 1.0 / (1.0 + np.exp(-acts[-1][:, 0, :]))
+
+
+def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One bias-corrected Adam step on the FP32 parameters (FP64 arithmetic)."""
+    p = np.asarray(params, np.float64)
+    g = np.asarray(grads, np.float64)
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    p = p - lr * (m / (1 - b1 ** step)) / (np.sqrt(v / (1 - b2 ** step)) + eps)
+    return p, m, v
+
+
+def comb(prob, bin_days, p_lo, p_hi, n_intervals):
+    """Period comb over per-bin maps prob [B][T] (bin widths bin_days [B] days), plain loops.
+
+    Interval q: edges lo = p_lo (p_hi/p_lo)^(q/n), hi = the same at q + 1, in bins
+    blo = lo / w, bhi = hi / w; trials Pb_m = blo + (bhi - blo)(m + 1/2) / nP with
+    nP = max(1, ceil((bhi - blo) T / blo)), skipped below 1 bin or above T; for each phase
+    ph < ceil(Pb) the epochs t_e = floor(ph + e Pb + 1/2) < T give sum_e p[t_e] / sqrt(E).
+    The interval's score is the largest such value, and 0 if none is positive.
+    """
+    import math
+    prob = np.asarray(prob, np.float64)
+    B, T = prob.shape
+    out = np.zeros((B, n_intervals))
+    for b in range(B):
+        w = float(bin_days[b])
+        if not w > 0.0:
+            continue
+        for q in range(n_intervals):
+            lo = p_lo * (p_hi / p_lo) ** (q / n_intervals)
+            hi = p_lo * (p_hi / p_lo) ** ((q + 1) / n_intervals)
+            blo, bhi = lo / w, hi / w
+            nP = max(1, math.ceil((bhi - blo) * T / blo))
+            best = 0.0
+            for m in range(nP):
+                Pb = blo + (bhi - blo) * (m + 0.5) / nP
+                if Pb < 1.0 or Pb > T:
+                    continue
+                for ph in range(math.ceil(Pb)):
+                    idx = []
+                    e = 0
+                    while True:
+                        t = math.floor(ph + e * Pb + 0.5)
+                        if t >= T:
+                            break
+                        idx.append(t)
+                        e += 1
+                    if idx:
+                        best = max(best, prob[b, idx].sum() / math.sqrt(len(idx)))
+            out[b, q] = best
+    return out

@@ -54,7 +54,9 @@ class cetra_batch_info(ctypes.Structure):
                 ("n_fold_items", ctypes.c_int64), ("fold_cell_reads", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("linear_threads", ctypes.c_int32),
                 ("fold_variant", ctypes.c_int32), ("fold_blocks", ctypes.c_int32),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("cadence", ctypes.c_double),
+                ("t0_step", ctypes.c_double), ("p", ctypes.c_int64), ("q", ctypes.c_int64),
+                ("n_pad", ctypes.c_int64)]
 
 
 class CetraError(RuntimeError):
@@ -105,6 +107,21 @@ SIGNATURES = {
     "cetra_batch_run": (_INT, [_P, _P, _P]),
     "cetra_batch_get_info": (_INT, [_P, ctypes.POINTER(cetra_batch_info)]),
     "cetra_batch_destroy": (None, [_P]),
+    "cetra_batch_features": (_INT, [_P, _P, _INT, _P]),
+    "cetra_batch_run_items": (_INT, [_P, _P, _P, _I64, _INT, _P]),
+    "cetra_batch_curve": (_INT, [_P, _INT, _P, _P, _P, _P, _P, _P]),
+    "cetra_cnn_create": (_INT, [_P, _INT, _INT, _INT, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "cetra_cnn_destroy": (None, [_P]),
+    "cetra_cnn_param_count": (_I64, [_P]),
+    "cetra_cnn_get_params": (_INT, [_P, _P, _P]),
+    "cetra_cnn_set_params": (_INT, [_P, _P, _P]),
+    "cetra_cnn_forward": (_INT, [_P, _P, _P, _INT, _P]),
+    "cetra_cnn_backward": (_INT, [_P, _P, _P, _P, _INT, ctypes.c_float,
+                                  ctypes.POINTER(ctypes.c_double), _P]),
+    "cetra_cnn_adam": (_INT, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float]),
+    "cetra_cnn_comb": (_INT, [_P, _P, _INT, _INT, _P, ctypes.c_double, ctypes.c_double, _INT,
+                              _P]),
     "cetra_search_batch": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
                                   _INT, _P, _INT, _P, _P, _P, _P]),
     "cetra_grid_get_info": (_INT, [_P, ctypes.POINTER(cetra_plan_info)]),

@@ -276,6 +276,20 @@ def cetra_periodic_search(ctx: Context, grid: LinearGrid, periods, mask=None) ->
 BEST_FIELDS = [f for f, _ in N.cetra_best._fields_]
 
 
+def batch_period_grid(period_min, ratio, n_periods):
+    """Periods 0 .. n_periods-1 of a batch curve: period_min * ratio^k with ratio^k by
+    LSB-first square-and-multiply in FP64 (the definition cetra_batch_create uses)."""
+    k = np.arange(int(n_periods), dtype=np.int64)
+    x = np.ones(k.size)
+    b = np.full(k.size, float(ratio))
+    m = k.copy()
+    while np.any(m):
+        x = np.where(m & 1, x * b, x)
+        b = b * b
+        m >>= 1
+    return float(period_min) * x
+
+
 def _best_dict(arr):
     return {f: np.array([getattr(b, f) for b in arr]) for f in BEST_FIELDS}
 
@@ -326,6 +340,34 @@ class Batch:
               "batch_run")
         return _best_dict(best) if results else None
 
+    def features(self, n_bins=4096):
+        """Max-pooled linear LR [n_curves][n_dur][n_bins] (torch CUDA tensor)."""
+        import torch
+        J = self.info["n_dur"]
+        out = torch.empty((self.n, J, n_bins), dtype=torch.float32,
+                          device=torch.device("cuda", self.ctx.device))
+        check(N.lib.cetra_batch_features(self.ctx.handle, self.handle, int(n_bins), _ptr(out)),
+              self.ctx.handle, "batch_features")
+        return out
+
+    def curve(self, c):
+        """(t_ref, period_min, ratio, n_periods, n_t0, first_item) of curve c."""
+        t_ref, pmin, rat = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        K, I, first = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        check(N.lib.cetra_batch_curve(self.handle, int(c), ctypes.byref(t_ref), ctypes.byref(pmin),
+                                      ctypes.byref(rat), ctypes.byref(K), ctypes.byref(I),
+                                      ctypes.byref(first)), self.ctx.handle, "batch_curve")
+        return t_ref.value, pmin.value, rat.value, K.value, I.value, first.value
+
+    def run_items(self, items, linear=True):
+        """Fold only the listed (curve, 8-period group) items; per-curve best."""
+        it = _np(items, np.int64)
+        best = (N.cetra_best * self.n)()
+        check(N.lib.cetra_batch_run_items(self.ctx.handle, self.handle, _ptr(it), it.size,
+                                          int(bool(linear)), best), self.ctx.handle,
+              "batch_run_items")
+        return _best_dict(best)
+
     def close(self):
         if self.handle:
             N.lib.cetra_batch_destroy(self.handle)
@@ -354,3 +396,66 @@ def cetra_search_batch(ctx: Context, curves, durations, tmpl, period_min, period
                                    _ptr(e), _ptr(d), d.size, _ptr(tm), tm.size, _ptr(pmin),
                                    _ptr(pmax), _ptr(rat), best), ctx.handle, "search_batch")
     return _best_dict(best)
+
+
+# ----------------------------------------------------------------------------- learned proposal
+
+class CNN:
+    """The period-interval proposal network (cetra_cnn_*)."""
+
+    def __init__(self, ctx: Context, in_channels, n_bins=4096, max_batch=64, seed=1):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p()
+        check(N.lib.cetra_cnn_create(ctx.handle, int(in_channels), int(n_bins), int(max_batch),
+                                     int(seed), ctypes.byref(self.handle)), ctx.handle,
+              "cnn_create")
+        self.n_params = int(N.lib.cetra_cnn_param_count(self.handle))
+        self.n_bins = n_bins
+        self.in_channels = in_channels
+        self.max_batch = max_batch
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        check(N.lib.cetra_cnn_get_params(self.ctx.handle, self.handle, _ptr(out)), self.ctx.handle)
+        return out
+
+    def set_params(self, params):
+        p = _np(params, np.float32)
+        assert p.size == self.n_params
+        check(N.lib.cetra_cnn_set_params(self.ctx.handle, self.handle, _ptr(p)), self.ctx.handle)
+
+    def forward(self, d_features, d_prob):
+        check(N.lib.cetra_cnn_forward(self.ctx.handle, self.handle, _ptr(d_features),
+                                      int(d_features.shape[0]), _ptr(d_prob)), self.ctx.handle,
+              "cnn_forward")
+
+    def backward(self, d_features, d_labels, pos_weight=20.0, grads=False):
+        loss = ctypes.c_double(0.0)
+        g = np.empty(self.n_params, np.float32) if grads else None
+        check(N.lib.cetra_cnn_backward(self.ctx.handle, self.handle, _ptr(d_features),
+                                       _ptr(d_labels), int(d_features.shape[0]),
+                                       float(pos_weight), ctypes.byref(loss), _ptr(g)),
+              self.ctx.handle, "cnn_backward")
+        return (loss.value, g) if grads else loss.value
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(N.lib.cetra_cnn_adam(self.ctx.handle, self.handle, float(lr), float(beta1),
+                                   float(beta2), float(eps)), self.ctx.handle, "cnn_adam")
+
+    def close(self):
+        if self.handle:
+            N.lib.cetra_cnn_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cetra_cnn_comb(ctx: Context, d_prob, d_bin_days, p_lo, p_hi, n_intervals, d_scores):
+    B, T = d_prob.shape
+    check(N.lib.cetra_cnn_comb(ctx.handle, _ptr(d_prob), int(B), int(T), _ptr(d_bin_days),
+                               float(p_lo), float(p_hi), int(n_intervals), _ptr(d_scores)),
+          ctx.handle, "cnn_comb")

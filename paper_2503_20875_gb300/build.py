@@ -1,12 +1,13 @@
 """Build the in-tree CUDA library ``libcetra.so`` for sm_103a (nvcc + g++, no cmake).
 
-Five translation units compiled in parallel and linked into one shared
+Six translation units compiled in parallel and linked into one shared
 library next to this file:
   csrc/kernels.cu  device kernels and their launchers  (nvcc, sm_103a)
   csrc/plan.cpp    host planner, FP64 index arithmetic  (g++, -ffp-contract=off)
   csrc/capi.cpp    the C ABI declared in include/cetra.h (g++)
   csrc/noalloc.cu  the allocation-free periodic entry point (nvcc)
   csrc/batch.cpp   the batched form: layout, CUDA graph, autotuner (g++)
+  csrc/cnn.cu      the learned period-interval proposal: CNN kernels and comb (nvcc)
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp"]
+SOURCES = ["kernels.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu"]
 
 
 def _cmd(src: str, obj: str) -> list[str]:

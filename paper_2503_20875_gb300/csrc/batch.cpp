@@ -40,6 +40,7 @@ struct cetra_batch {
     unsigned long long *d_keys = nullptr, *d_pkeys = nullptr;
     cetra_best *d_best = nullptr;
     int *d_queue = nullptr, *d_status = nullptr;
+    int64_t *d_items = nullptr;  // explicit fold work list (cetra_batch_run_items)
 };
 
 namespace {
@@ -76,51 +77,60 @@ int64_t build_tiles(cetra_batch *b, int threads) {
     return b->tile_off.back();
 }
 
-// Algorithmic (A, B) reads of the fold of one curve (same count as the single-curve bench).
+// Algorithmic (A, B) reads of the fold of one curve: about I reads per (period, duration
+// D < P) (each t0 cell belongs to one (phase, epoch) of a period, up to the rounding of
+// the epoch offsets at the ends).
 int64_t fold_reads(const cetra_plan *plan, const batch_curve &cv) {
     int64_t total = 0;
-    const int64_t I = cv.I;
+    std::vector<double> d(plan->durations);
+    std::sort(d.begin(), d.end());
     for (int64_t k = 0; k < cv.n_periods; ++k) {
         const double P = batch_period_host(cv.pmin, cv.ratio, k);
         const double Ps = (P * (double)plan->q) / (plan->cadence * (double)plan->p);
         if (!(Ps >= 1.0)) continue;
-        const int64_t nph = std::min<int64_t>(I, (int64_t)std::ceil(Ps));
-        int64_t cells = 0;
-        for (int64_t e = 0;; ++e) {
-            const int64_t o = (int64_t)std::floor((double)e * Ps + 0.5);
-            if (o >= I) break;
-            cells += std::min<int64_t>(nph, I - o);
-        }
-        int nd = 0;
-        for (double D : plan->durations) nd += D < P;
-        total += cells * nd;
+        const int64_t nd = std::lower_bound(d.begin(), d.end(), P) - d.begin();
+        total += (int64_t)cv.I * nd;
     }
     return total;
 }
 
-cudaError_t enqueue(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads) {
+// The stages before the fold: clear, resample, linear search.
+cudaError_t enqueue_linear(cetra_batch *b, int lin_threads) {
     cetra_plan *plan = b->plan;
     cudaStream_t st = b->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(b->d_wy, 0, (size_t)b->n_cells * sizeof(float), st))) return e;
     if ((e = cudaMemsetAsync(b->d_w, 0, (size_t)b->n_cells * sizeof(float), st))) return e;
     if ((e = cudaMemsetAsync(b->d_ab, 0, (size_t)b->ab_cells * sizeof(float2), st))) return e;
-    if ((e = cudaMemsetAsync(b->d_keys, 0, (size_t)b->n_curves * sizeof(unsigned long long), st)))
-        return e;
-    if ((e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st))) return e;  // queue, status
     if ((e = launch_batch_resample(st, b->ctx->num_sms, plan, b->d_time, b->d_flux, b->d_err,
                                    b->n_points, b->d_pt_off, b->n_curves, b->d_curves, b->d_wy,
                                    b->d_w)))
         return e;
-    if ((e = launch_batch_linear(st, plan, lin_threads, b->d_tile_off, b->n_curves, b->n_tiles,
-                                 b->d_curves, b->d_wy, b->d_w, b->d_ab)))
+    return launch_batch_linear(st, plan, lin_threads, b->d_tile_off, b->n_curves, b->n_tiles,
+                               b->d_curves, b->d_wy, b->d_w, b->d_ab);
+}
+
+// The fold over n_items work items (item_list NULL: items 0 .. n_items-1) and the finalize.
+cudaError_t enqueue_fold(cetra_batch *b, int64_t n_items, int fold_variant,
+                         const int64_t *item_list) {
+    cetra_plan *plan = b->plan;
+    cudaStream_t st = b->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->d_keys, 0, (size_t)b->n_curves * sizeof(unsigned long long), st)))
         return e;
+    if ((e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st))) return e;  // queue, status
     if ((e = launch_batch_fold(st, b->fold_blocks, fold_variant, plan, b->d_ab, b->d_curves,
                                b->d_group_off, b->n_curves, n_items, b->d_queue, b->d_pkeys,
-                               b->d_keys, b->d_status)))
+                               b->d_keys, b->d_status, item_list)))
         return e;
     return launch_batch_finalize(st, plan, b->d_ab, b->d_curves, b->n_curves, b->d_pkeys,
                                  b->d_keys, b->d_status, b->d_best);
+}
+
+cudaError_t enqueue(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads) {
+    cudaError_t e = enqueue_linear(b, lin_threads);
+    if (e) return e;
+    return enqueue_fold(b, n_items, fold_variant, nullptr);
 }
 
 // Milliseconds of one enqueue() with the given shapes (the batch is rebuilt by the caller).
@@ -297,7 +307,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     // device memory, one allocation carved in 256-byte aligned pieces
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0, o_time, o_flux, o_err, o_wy, o_w, o_ab, o_pt, o_tile, o_grp, o_cv, o_keys,
-                    o_pkeys, o_best, o_q;
+                    o_pkeys, o_best, o_q, o_items;
     o_time = off; off = up(off + (size_t)n_points * sizeof(double));
     o_flux = off; off = up(off + (size_t)n_points * sizeof(float));
     o_err = off; off = up(off + (size_t)n_points * sizeof(float));
@@ -312,6 +322,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_pkeys = off; off = up(off + (size_t)std::max<int64_t>(per, 1) * sizeof(unsigned long long));
     o_best = off; off = up(off + (size_t)n_curves * sizeof(cetra_best));
     o_q = off; off = up(off + 2 * sizeof(int));
+    o_items = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1) * sizeof(int64_t));
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e) return bail(cuda_fail(ctx, e, "batch device"));
     e = cudaMalloc(&b->d_mem, off);
@@ -336,6 +347,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     b->d_best = reinterpret_cast<cetra_best *>(base + o_best);
     b->d_queue = reinterpret_cast<int *>(base + o_q);
     b->d_status = b->d_queue + 1;
+    b->d_items = reinterpret_cast<int64_t *>(base + o_items);
 
     if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) ||
         (e = cudaEventCreate(&b->ev_start)) || (e = cudaEventCreate(&b->ev_stop)))
@@ -397,6 +409,64 @@ int cetra_batch_run(cetra_ctx *ctx, cetra_batch *b, cetra_best *best) {
     return CETRA_OK;
 }
 
+int cetra_batch_features(cetra_ctx *ctx, cetra_batch *b, int n_bins, float *d_features) {
+    if (!ctx || !b || !d_features || n_bins < 1)
+        return set_error(ctx, CETRA_EINVAL, "batch_features: bad argument");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
+    if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
+    if (!e) e = enqueue_linear(b, b->lin_threads);
+    if (!e) e = launch_batch_features(b->stream, ctx->num_sms, b->plan, b->d_ab, b->d_curves,
+                                      b->n_curves, n_bins, d_features);
+    if (!e) e = cudaStreamSynchronize(b->stream);
+    if (e) return cuda_fail(ctx, e, "batch_features");
+    ctx->launches += 3;
+    return CETRA_OK;
+}
+
+int cetra_batch_run_items(cetra_ctx *ctx, cetra_batch *b, const int64_t *items, int64_t n_items,
+                          int linear, cetra_best *best) {
+    if (!ctx || !b || n_items < 0 || (n_items > 0 && !items))
+        return set_error(ctx, CETRA_EINVAL, "batch_run_items: bad argument");
+    if (n_items > b->n_items)
+        return set_error(ctx, CETRA_ECAPACITY, "batch_run_items: more items than the batch has");
+    for (int64_t x = 0; x < n_items; ++x)
+        if (items[x] < 0 || items[x] >= b->n_items)
+            return set_error(ctx, CETRA_EINVAL, "batch_run_items: item out of range");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
+    if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
+    if (!e && n_items)
+        e = cudaMemcpyAsync(b->d_items, items, (size_t)n_items * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (!e && linear) e = enqueue_linear(b, b->lin_threads);
+    if (!e) e = enqueue_fold(b, n_items, b->fold_variant, b->d_items);
+    int status = 0;
+    if (!e && best)
+        e = cudaMemcpyAsync(best, b->d_best, (size_t)b->n_curves * sizeof(cetra_best),
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaStreamSynchronize(b->stream);
+    if (e) return cuda_fail(ctx, e, "batch_run_items");
+    ctx->launches += linear ? 4 : 2;
+    if (status != 0) return set_error(ctx, CETRA_ETIMEOUT, "batch_run_items: a device wait timed out");
+    return CETRA_OK;
+}
+
+int cetra_batch_curve(const cetra_batch *b, int curve, double *t_ref, double *period_min,
+                      double *period_ratio, int32_t *n_periods, int32_t *n_t0,
+                      int64_t *first_item) {
+    if (!b || curve < 0 || curve >= b->n_curves) return CETRA_EINVAL;
+    const batch_curve &cv = b->curves[curve];
+    if (t_ref) *t_ref = cv.t_ref;
+    if (period_min) *period_min = cv.pmin;
+    if (period_ratio) *period_ratio = cv.ratio;
+    if (n_periods) *n_periods = cv.n_periods;
+    if (n_t0) *n_t0 = cv.I;
+    if (first_item) *first_item = b->group_off[curve];
+    return CETRA_OK;
+}
+
 int cetra_batch_get_info(const cetra_batch *b, cetra_batch_info *info) {
     if (!b || !info) return CETRA_EINVAL;
     info->n_curves = b->n_curves;
@@ -412,6 +482,11 @@ int cetra_batch_get_info(const cetra_batch *b, cetra_batch_info *info) {
     info->fold_variant = b->fold_variant;
     info->fold_blocks = b->fold_blocks;
     info->graph = b->graph != nullptr;
+    info->cadence = b->plan->cadence;
+    info->t0_step = b->plan->t0_step;
+    info->p = b->plan->p;
+    info->q = b->plan->q;
+    info->n_pad = b->plan->n_pad;
     return CETRA_OK;
 }
 

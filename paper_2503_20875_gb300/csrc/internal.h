@@ -155,7 +155,11 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const float2 *ab, const batch_curve *curves,
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
-                              unsigned long long *curve_keys, int *status);
+                              unsigned long long *curve_keys, int *status,
+                              const int64_t *item_list);
+cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_plan *plan,
+                                  const float2 *ab, const batch_curve *curves, int n_curves,
+                                  int n_bins, float *out);
 cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
                                   const batch_curve *curves, int n_curves,
                                   const unsigned long long *period_keys,

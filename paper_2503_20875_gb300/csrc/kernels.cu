@@ -1002,7 +1002,8 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                   const int64_t *__restrict__ group_off, int n_curves, int64_t n_items, int J,
                   const double *__restrict__ durations, double c, int64_t p, int64_t q,
                   int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
-                  unsigned long long *__restrict__ curve_keys, int *__restrict__ status) {
+                  unsigned long long *__restrict__ curve_keys, int *__restrict__ status,
+                  const int64_t *__restrict__ item_list) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *strips = reinterpret_cast<float2 *>(smem_raw);
     int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);
@@ -1015,8 +1016,9 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
         __syncthreads();  // the previous item is done with the shared state
         if (t == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
-        const int64_t item = s_item;
-        if (item >= n_items) break;
+        if (s_item >= n_items) break;
+        // queue position -> work item: the position itself, or the caller's list entry
+        const int64_t item = item_list ? item_list[s_item] : (int64_t)s_item;
         const int cidx = csr_find(group_off, n_curves, item);
         const batch_curve cv = curves[cidx];
         const int k0 = (int)(item - group_off[cidx]) * FT_G;
@@ -1091,6 +1093,34 @@ __global__ void batch_finalize_kernel(const float2 *__restrict__ ab,
     out.i = i;
     out.j = j;
     best[cidx] = out;
+}
+
+// Linear-search features of every batch curve: the window LR = A^2 / (2B) (Sec. 2.2) of
+// the windows with a positive depth (A > 0: a dimming), max-pooled over n_bins equal bins
+// of the curve's t0 grid (bin width ceil(I / n_bins)); empty bins, null windows and
+// brightenings give 0. Layout [curve][duration][bin].
+__global__ void batch_features_kernel(const float2 *__restrict__ ab,
+                                      const batch_curve *__restrict__ curves, int n_curves, int J,
+                                      int n_bins, float *__restrict__ out) {
+    const int64_t total = (int64_t)n_curves * J * n_bins;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+        const int bin = (int)(x % n_bins);
+        const int j = (int)((x / n_bins) % J);
+        const int cidx = (int)(x / ((int64_t)n_bins * J));
+        const batch_curve cv = curves[cidx];
+        float m = 0.0f;
+        if (cv.I > 0) {
+            const int width = (cv.I + n_bins - 1) / n_bins;
+            const int lo = bin * width, hi = min(cv.I, lo + width);
+            const float2 *row = ab + cv.ab_off + (int64_t)j * cv.ld;
+            for (int i = lo; i < hi; ++i) {
+                const float2 v = row[i];
+                if (v.y > 0.0f && v.x > 0.0f) m = fmaxf(m, 0.5f * (v.x * (v.x / v.y)));
+            }
+        }
+        out[x] = m;
+    }
 }
 
 }  // namespace
@@ -1263,7 +1293,8 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const float2 *ab, const batch_curve *curves,
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
-                              unsigned long long *curve_keys, int *status) {
+                              unsigned long long *curve_keys, int *status,
+                              const int64_t *item_list) {
     if (n_items <= 0) return cudaSuccess;
     auto kern = batch_fold_kernel<false, FT_R>;
     if (plan->precision == CETRA_FP32_KAHAN)
@@ -1272,7 +1303,7 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
         kern = batch_fold_kernel<false, FT_R / 2>;
     kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
         ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
-        plan->p, plan->q, queue, period_keys, curve_keys, status);
+        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list);
     return cudaGetLastError();
 }
 
@@ -1303,4 +1334,17 @@ cudaError_t batch_configure(const cetra_plan *plan) {
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_plan *plan,
+                                  const float2 *ab, const batch_curve *curves, int n_curves,
+                                  int n_bins, float *out) {
+    const int64_t total = (int64_t)n_curves * plan->J * n_bins;
+    if (total <= 0) return cudaSuccess;
+    const int threads = 256;
+    int64_t blocks = (total + threads - 1) / threads;
+    if (blocks > (int64_t)num_sms * 32) blocks = (int64_t)num_sms * 32;
+    batch_features_kernel<<<(unsigned)blocks, threads, 0, stream>>>(ab, curves, n_curves, plan->J,
+                                                                     n_bins, out);
+    return cudaGetLastError();
 }

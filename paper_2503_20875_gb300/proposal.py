@@ -1,0 +1,171 @@
+"""Learned period-interval proposal for the batched search (not in the paper).
+
+The periodic search (Sec. 2.3) folds every trial period; this aid picks, per curve, a small
+fraction of log-spaced period intervals to fold instead:
+  1. cetra_batch_features: every window's LR (positive depths), max-pooled to
+     [durations][n_bins] per curve.
+  2. cetra_cnn_forward: per-bin probability that a bin holds a transit.
+  3. cetra_cnn_comb: a score for each period interval from that map.
+  4. each curve's best intervals -> the fold work items (8-period groups) of their periods
+     -> cetra_batch_run_items: the fold over those periods only.
+The network is trained on injection curves: the labels mark the bins that hold an injected
+transit (its mid-time +- half its duration). Every step of the arithmetic runs in the
+library's kernels; this module only does the bookkeeping on the host.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .api import Batch, CNN, Context, batch_period_grid, cetra_cnn_comb
+
+N_BINS = 4096
+N_INTERVALS = 512
+P_LO = 0.5
+GROUP = 8   # periods per fold work item
+
+
+# --------------------------------------------------------------------------- host bookkeeping
+
+def geometry(batch: Batch):
+    """Per curve: (t_ref, period_min, ratio, n_periods, n_t0, first_item)."""
+    return [batch.curve(c) for c in range(batch.n)]
+
+
+def t0_index(t, t_ref, info):
+    """Position of time t on a curve's t0 grid: t0_i = t_ref + (i p / q - n_pad) cadence."""
+    return (t - t_ref) / info["t0_step"] + info["n_pad"] * info["q"] / info["p"]
+
+
+def labels(geo, info, planets_per_curve, n_bins=N_BINS):
+    """[n_curves][n_bins] float32: 1 for the bins of each curve's t0 grid that hold an
+    injected transit (any t0 within D/2 of a transit mid-time), else 0."""
+    out = np.zeros((len(geo), n_bins), np.float32)
+    for idx, (g, planets) in enumerate(zip(geo, planets_per_curve)):
+        t_ref, I = g[0], g[4]
+        if I <= 0:
+            continue
+        width = (I + n_bins - 1) // n_bins
+        s = info["t0_step"]
+        i_last = I - 1
+        for pl in planets:
+            P, t0, D = pl["P"], pl["t0"], pl["D"]
+            # mid-times t0 + n P whose +-D/2 span meets the grid (index 0 .. I - 1)
+            t_first = t_ref - info["n_pad"] * info["cadence"]
+            t_last = t_first + i_last * s
+            n_lo = math.floor((t_first - 0.5 * D - t0) / P)
+            n_hi = math.ceil((t_last + 0.5 * D - t0) / P)
+            for n in range(n_lo, n_hi + 1):
+                ic = t0_index(t0 + n * P, t_ref, info)
+                hw = 0.5 * D / s
+                lo, hi = max(math.ceil(ic - hw), 0), min(math.floor(ic + hw), i_last)
+                if lo <= hi:
+                    out[idx, lo // width:hi // width + 1] = 1.0
+    return out
+
+
+def bin_days(geo, info, n_bins=N_BINS):
+    """Width in days of one feature bin of each curve (0 for a curve without t0 cells)."""
+    s = info["t0_step"]
+    return np.array([((g[4] + n_bins - 1) // n_bins) * s if g[4] > 0 else 0.0 for g in geo],
+                    np.float64)
+
+
+def interval_edges(p_hi, n_intervals=N_INTERVALS):
+    """Edges (days) of the log-spaced intervals the comb scores."""
+    return P_LO * (p_hi / P_LO) ** (np.arange(n_intervals + 1) / n_intervals)
+
+
+def period_intervals(g, p_hi, n_intervals=N_INTERVALS):
+    """Interval index of each trial period of one curve (geometry g)."""
+    _, pmin, ratio, K, _, _ = g
+    P = batch_period_grid(pmin, ratio, K)
+    q = np.searchsorted(interval_edges(p_hi, n_intervals), P, side="right") - 1
+    return np.clip(q, 0, n_intervals - 1)
+
+
+def items_from_scores(geo, scores, p_hi, top_frac=0.05, n_intervals=N_INTERVALS):
+    """Fold work items of the periods in each curve's best intervals.
+
+    Per curve, of the intervals its period grid reaches, the ceil(top_frac x their number)
+    with the highest scores (ties: lower interval first) are kept; an item is one group of
+    GROUP consecutive periods, kept when any of its periods lies in a kept interval.
+    Returns (items int64, kept-period count)."""
+    items, n_periods = [], 0
+    for c, g in enumerate(geo):
+        K, first = g[3], g[5]
+        if K <= 0:
+            continue
+        q = period_intervals(g, p_hi, n_intervals)
+        present = np.unique(q)
+        n_keep = max(1, int(math.ceil(top_frac * present.size)))
+        keep = present[np.argsort(-np.asarray(scores[c])[present], kind="stable")[:n_keep]]
+        groups = np.unique(np.nonzero(np.isin(q, keep))[0] // GROUP)
+        n_periods += int(sum(min(GROUP, K - GROUP * x) for x in groups))
+        items.append(first + groups)
+    return (np.concatenate(items).astype(np.int64) if items else np.zeros(0, np.int64),
+            n_periods)
+
+
+def period_max(geo):
+    """Upper edge for the intervals: just above the longest trial period of the batch."""
+    top = [g[1] * g[2] ** (g[3] - 1) for g in geo if g[3] > 0]
+    return max(top) * (1.0 + 1e-9) if top else 2.0 * P_LO
+
+
+def random_items(geo, p_hi, top_frac, seed, n_intervals=N_INTERVALS):
+    """The same budget as items_from_scores with intervals drawn uniformly at random."""
+    rng = np.random.default_rng(seed)
+    scores = rng.uniform(size=(len(geo), n_intervals))
+    return items_from_scores(geo, scores, p_hi, top_frac, n_intervals)
+
+
+# --------------------------------------------------------------------------- device steps
+
+def train(cnn: CNN, d_features, d_labels, epochs=3, batch_size=32, lr=2e-3, pos_weight=20.0,
+          seed=0):
+    """Adam over mini-batches of curves; returns the mean loss of each epoch."""
+    n = d_features.shape[0]
+    rng = np.random.default_rng(seed)
+    history = []
+    for _ in range(epochs):
+        losses = []
+        for blk in rng.permutation(n // batch_size):
+            a, b = blk * batch_size, (blk + 1) * batch_size
+            losses.append(cnn.backward(d_features[a:b], d_labels[a:b], pos_weight))
+            cnn.adam(lr)
+        history.append(float(np.mean(losses)))
+    return history
+
+
+def predict(cnn: CNN, d_features, chunk=None):
+    """Per-bin transit probabilities [n_curves][n_bins] (torch CUDA tensor)."""
+    import torch
+    n = d_features.shape[0]
+    chunk = chunk or cnn.max_batch
+    out = torch.empty((n, d_features.shape[2]), dtype=torch.float32, device=d_features.device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        cnn.forward(d_features[a:b], out[a:b])
+    return out
+
+
+def interval_scores(ctx: Context, geo, info, d_maps, p_hi, n_intervals=N_INTERVALS):
+    """Comb scores [n_curves][n_intervals] of per-bin maps d_maps (host numpy)."""
+    import torch
+    bw = torch.as_tensor(bin_days(geo, info, d_maps.shape[1]), device=d_maps.device)
+    scores = torch.empty((d_maps.shape[0], n_intervals), dtype=torch.float32,
+                         device=d_maps.device)
+    cetra_cnn_comb(ctx, d_maps.contiguous(), bw, P_LO, p_hi, n_intervals, scores)
+    return scores.cpu().numpy()
+
+
+def propose_and_fold(ctx: Context, batch: Batch, d_maps, p_hi, top_frac=0.05,
+                     n_intervals=N_INTERVALS):
+    """Comb the maps, fold each curve's best intervals; returns (best dict, items, n_periods).
+    The batch's linear stage must be current (cetra_batch_features ran on it)."""
+    geo = geometry(batch)
+    scores = interval_scores(ctx, geo, batch.info, d_maps, p_hi, n_intervals)
+    items, n_per = items_from_scores(geo, scores, p_hi, top_frac, n_intervals)
+    return batch.run_items(items, linear=False), items, n_per

@@ -177,12 +177,14 @@ def make_workload(name, seed=1, **kw):
     return WORKLOADS[name](seed=seed, **kw)
 
 
-def make_batch_workload(n_curves=8192, seed=1, max_sectors=13):
+def make_batch_workload(n_curves=8192, seed=1, max_sectors=13, planet_frac=0.3,
+                        snr_range=(5.0, 20.0), min_sectors=1):
     """Batch of uneven 30-min curves: S ~ U{1..13} sectors of 27.4 d with 1-d gaps.
 
     Per-curve sigma_c log-uniform 500-5,000 ppm, per-point sigma = sigma_c
-    exp(0.2 N(0, 1)); 30 % of curves carry one planet with P log-uniform in
-    [1, min(100, T/2)] d and SNR ~ U(5, 20), depth = SNR sigma_c / sqrt(n_in).
+    exp(0.2 N(0, 1)); a fraction planet_frac (30 %) of curves carries one planet
+    with P log-uniform in [1, min(100, T/2)] d and SNR ~ U(snr_range) (5-20),
+    depth = SNR sigma_c / sqrt(n_in).
     Returns a list of Workload (16 log-spaced durations 1-16 h, t0 step 10 min,
     periods log-spaced from 0.5 d to T/2 with ratio 1 + D_min / (2 T)).
     """
@@ -191,7 +193,7 @@ def make_batch_workload(n_curves=8192, seed=1, max_sectors=13):
     out = []
     durations = log_grid(1.0 * HOUR, 16.0 * HOUR, 16)
     for c in range(n_curves):
-        S = int(rng.integers(1, max_sectors + 1))
+        S = int(rng.integers(min_sectors, max_sectors + 1))
         segs = []
         start = 0.0
         for _ in range(S):
@@ -203,10 +205,10 @@ def make_batch_workload(n_curves=8192, seed=1, max_sectors=13):
         sig_c = float(np.exp(rng.uniform(np.log(500e-6), np.log(5000e-6))))
         sig = sig_c * np.exp(0.2 * rng.normal(size=t.size))
         planets = []
-        if rng.uniform() < 0.3:
+        if rng.uniform() < planet_frac:
             P = float(np.exp(rng.uniform(np.log(1.0), np.log(min(100.0, T / 2.0)))))
             D = 13.0 * HOUR * (P / 365.0) ** (1.0 / 3.0)
-            snr = float(rng.uniform(5.0, 20.0))
+            snr = float(rng.uniform(*snr_range))
             n_in = max(1.0, (T / P) * D / cad)
             planets.append(dict(P=P, t0=float(rng.uniform(0.0, P)), D=D,
                                 depth=snr * sig_c / np.sqrt(n_in), b=0.3, u1=0.4804, u2=0.1867,

@@ -1,0 +1,123 @@
+"""Pins of the FP64 network reference (oracle/cnn.py) against library routines and
+finite differences: it is then the yardstick for the CUDA proposal network."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+
+def test_conv_is_cross_correlation():
+    rng = np.random.default_rng(0)
+    from scipy.signal import correlate
+    x = rng.normal(size=(1, 1, 50))
+    W = rng.normal(size=(1, 1, 9))
+    y, _ = cnn.conv(x, W, np.zeros(1))
+    ref = correlate(x[0, 0], W[0, 0], mode="same")
+    np.testing.assert_allclose(y[0, 0], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    w = np.concatenate([rng.normal(size=1000).astype(np.float32),
+                        np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -2.5e-3], np.float32)])
+    ref = torch.from_numpy(w).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(cnn.bf16_round(w), ref)
+    assert cnn.bf16_round(np.float32(1 + 2 ** -8)) == 1.0  # a tie goes to even
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(2)
+    B, cin, T = 2, 3, 40
+    f = rng.exponential(3.0, size=(B, cin, T)).astype(np.float32)
+    y = (rng.uniform(size=(B, T)) < 0.1).astype(np.float64)
+    layers = []
+    for o, i in cnn.shapes(cin):
+        layers.append((rng.normal(0, 0.4, size=(o, i, cnn.K)), rng.normal(0, 0.1, size=o)))
+    loss, flat = cnn.loss_and_grads_layers(layers, f, y, 4.0)
+    # central differences on a sample of weights and biases of every layer
+    off = 0
+    h = 1e-6
+    for l, (W, b) in enumerate(layers):
+        for idx in list(zip(*[rng.integers(0, s, 4) for s in W.shape])):
+            Wp = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wm = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wp[l][0][idx] += h
+            Wm[l][0][idx] -= h
+            num = (cnn.loss_and_grads_layers(Wp, f, y, 4.0)[0] -
+                   cnn.loss_and_grads_layers(Wm, f, y, 4.0)[0]) / (2 * h)
+            ana = flat[off + np.ravel_multi_index(idx, W.shape)]
+            assert ana == pytest.approx(num, rel=1e-5, abs=1e-9)
+        off += W.size
+        for o in range(min(2, b.size)):
+            Wp = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wm = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wp[l][1][o] += h
+            Wm[l][1][o] -= h
+            num = (cnn.loss_and_grads_layers(Wp, f, y, 4.0)[0] -
+                   cnn.loss_and_grads_layers(Wm, f, y, 4.0)[0]) / (2 * h)
+            assert flat[off + o] == pytest.approx(num, rel=1e-5, abs=1e-9)
+        off += b.size
+
+
+def test_loss_closed_form():
+    """Zero weights and biases: every logit is 0, loss = log 2 (w+ p + 1 - p), p the label rate."""
+    rng = np.random.default_rng(3)
+    f = rng.exponential(size=(2, 2, 30)).astype(np.float32)
+    y = (rng.uniform(size=(2, 30)) < 0.2).astype(np.float64)
+    layers = [(np.zeros((o, i, cnn.K)), np.zeros(o)) for o, i in cnn.shapes(2)]
+    loss, _ = cnn.loss_and_grads_layers(layers, f, y, 3.0)
+    assert loss == pytest.approx(np.log(2) * (3.0 * y.mean() + 1 - y.mean()), rel=1e-12)
+
+
+def test_adam_matches_torch():
+    """Three bias-corrected Adam steps equal torch.optim.Adam's."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    p0 = rng.normal(size=50)
+    grads = [rng.normal(size=50) for _ in range(3)]
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for step, g in enumerate(grads, 1):
+        t.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        p, m, v = cnn.adam_step(p, g, m, v, step, 1e-2)
+    np.testing.assert_allclose(p, t.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_comb_constant_map_closed_form():
+    """A map of ones: every (trial, phase) scores sqrt(E), the largest E at phase 0 of the
+    shortest trial of the interval, E = ceil((T - 1/2) / Pb)."""
+    import math
+    T, w, n = 300, 0.1, 12
+    sc = cnn.comb(np.ones((1, T)), [w], 0.5, 12.0, n)
+    for q in range(n):
+        lo = 0.5 * (12.0 / 0.5) ** (q / n) / w
+        hi = 0.5 * (12.0 / 0.5) ** ((q + 1) / n) / w
+        nP = max(1, math.ceil((hi - lo) * T / lo))
+        P0 = lo + (hi - lo) * 0.5 / nP
+        assert sc[0, q] == pytest.approx(math.sqrt(math.ceil((T - 0.5) / P0)), rel=1e-12)
+
+
+def test_comb_finds_planted_pulse_train():
+    """Twenty one-bin pulses every 50 bins from bin 7: the interval holding 50 bins scores
+    sqrt(20) (all pulses on one trial), the best of all intervals; the intervals holding the
+    half (20 hits of 40 epochs) and the double (10 of 10) score sqrt(10)."""
+    import math
+    T = 1000
+    m = np.zeros((1, T))
+    m[0, 7::50] = 1.0
+    lo, hi, n = 10.0, 400.0, 64
+    sc = cnn.comb(m, [1.0], lo, hi, n)[0]
+    qi = int(math.floor(n * math.log(50.0 / lo) / math.log(hi / lo)))
+    assert sc[qi] == pytest.approx(math.sqrt(20.0), rel=1e-12)
+    assert np.argmax(sc) == qi
+    for P in (25.0, 100.0):
+        qh = int(math.floor(n * math.log(P / lo) / math.log(hi / lo)))
+        assert sc[qh] == pytest.approx(math.sqrt(10.0), rel=1e-12)
+
+
+def test_comb_null_curve_scores_zero():
+    sc = cnn.comb(np.ones((2, 64)), [0.0, -1.0], 0.5, 5.0, 4)
+    assert np.all(sc == 0.0)

@@ -1,0 +1,86 @@
+"""Host bookkeeping of the learned period-interval proposal (no GPU): transit labels on the
+t0 grid, interval membership of trial periods, and the fold work items a score table keeps."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_20875_gb300 import proposal
+from paper_2503_20875_gb300.api import batch_period_grid
+
+INFO = dict(cadence=0.01, t0_step=0.02, p=2, q=1, n_pad=5)
+
+
+def _brute_labels(t_ref, I, planets, n_bins):
+    """Label every t0 cell by its own time (t_i = t_ref + i s - n_pad c), then max-pool."""
+    s, c = INFO["t0_step"], INFO["cadence"]
+    width = (I + n_bins - 1) // n_bins
+    out = np.zeros(n_bins, np.float32)
+    for i in range(I):
+        t = t_ref + i * s - INFO["n_pad"] * c
+        for pl in planets:
+            n = round((t - pl["t0"]) / pl["P"])
+            if any(abs(t - (pl["t0"] + m * pl["P"])) <= 0.5 * pl["D"] + 1e-12
+                   for m in (n - 1, n, n + 1)):
+                out[i // width] = 1.0
+    return out
+
+
+@pytest.mark.parametrize("t_ref,I,n_bins", [(0.0, 1000, 100), (12.3, 777, 64), (5.0, 50, 256)])
+def test_labels_match_cell_by_cell(t_ref, I, n_bins):
+    planets = [dict(P=3.0, t0=t_ref + 1.0, D=0.1), dict(P=2.2, t0=t_ref - 7.05, D=0.23)]
+    geo = [(t_ref, 0.5, 1.001, 10, I, 0), (t_ref, 0.5, 1.001, 0, 0, 2)]
+    got = proposal.labels(geo, INFO, [planets, planets], n_bins)
+    np.testing.assert_array_equal(got[0], _brute_labels(t_ref, I, planets, n_bins))
+    assert not got[1].any()  # a curve without t0 cells has no labels
+
+
+def test_bin_days_and_period_max():
+    geo = [(0.0, 0.5, 1.001, 100, 1000, 0), (0.0, 0.5, 1.002, 0, 0, 13), (0.0, 0.7, 1.01, 3, 9000, 13)]
+    bw = proposal.bin_days(geo, INFO, 4096)
+    np.testing.assert_allclose(bw, [1 * 0.02, 0.0, 3 * 0.02])
+    pmax = proposal.period_max(geo)
+    assert pmax >= max(batch_period_grid(0.5, 1.001, 100)[-1], batch_period_grid(0.7, 1.01, 3)[-1])
+    assert pmax <= 0.7 * 1.01 ** 2 * (1 + 1e-8)
+
+
+def test_items_keep_the_best_intervals():
+    K, first = 1000, 40
+    geo = [(0.0, 0.5, 1.003, K, 5000, first)]
+    p_hi = proposal.period_max(geo)
+    n_int = 64
+    q = proposal.period_intervals(geo[0], p_hi, n_int)
+    P = batch_period_grid(0.5, 1.003, K)
+    edges = proposal.interval_edges(p_hi, n_int)
+    assert np.all(edges[q] <= P) and np.all(P < edges[q + 1])
+    present = np.unique(q)
+    scores = np.zeros((1, n_int))
+    scores[0, present[5]] = 3.0
+    scores[0, present[-1]] = 2.0
+    scores[0, present[0]] = 1.0
+    items, n_per = proposal.items_from_scores(geo, scores, p_hi, top_frac=2.5 / present.size,
+                                              n_intervals=n_int)
+    want = np.unique(np.nonzero(np.isin(q, present[[5, -1, 0]]))[0] // 8) + first
+    np.testing.assert_array_equal(items, want)
+    assert n_per == sum(min(8, K - 8 * (x - first)) for x in want)
+    assert items.min() >= first and items.max() < first + math.ceil(K / 8)
+
+
+def test_items_budget_and_empty_curves():
+    geo = [(0.0, 0.5, 1.001, 3000, 4000, 0), (0.0, 0.5, 1.001, 0, 0, 375),
+           (0.0, 0.6, 1.002, 700, 4000, 375)]
+    p_hi = proposal.period_max(geo)
+    items, n_per = proposal.random_items(geo, p_hi, 0.05, seed=1)
+    assert np.all(np.diff(items) > 0)  # sorted, unique
+    for g in (geo[0], geo[2]):
+        K, first = g[3], g[5]
+        q = proposal.period_intervals(g, p_hi)
+        n_keep = math.ceil(0.05 * np.unique(q).size)
+        mine = items[(items >= first) & (items < first + math.ceil(K / 8))] - first
+        covered = np.zeros(K, bool)
+        for x in mine:
+            covered[8 * x:8 * x + 8] = True
+        full = [v for v in np.unique(q) if covered[q == v].all()]
+        assert len(full) >= n_keep  # the kept intervals are folded in full
+        for x in mine:  # and every kept group serves one of them
+            assert np.isin(q[8 * x:8 * x + 8], full).any()
