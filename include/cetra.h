@@ -398,18 +398,27 @@ int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features,
 /* One Adam step with the last gradient (bias-corrected), then re-rounds the BF16 weights. */
 int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *cnn, float lr, float beta1, float beta2,
                    float eps);
+/* Proposal map d_map[b][t] = d_prob[b][t] * sqrt(2 max_j max(d_features[b][j][t], 0)): the
+ * network's transit probability times the bin's best window SNR (window LR = SNR^2/2,
+ * Sec. 2.2). d_prob, d_map: device FP32 [B][n_bins]; d_features: device FP32
+ * [B][n_dur][n_bins] (cetra_batch_features). Asynchronous on the context's stream. */
+int cetra_cnn_map(cetra_ctx *ctx, const float *d_prob, const float *d_features, int B,
+                  int n_dur, int n_bins, float *d_map);
 /* Comb scores of n_intervals log-spaced period intervals between p_lo and p_hi days for each
- * of B per-bin maps d_prob [B][n_bins] (bin widths d_bin_days [B] days, device FP64): the
- * best, over trial periods and phases, of sum_e p(t_e) / sqrt(E) with
- * t_e = floor(phase + e P + 1/2) < n_bins. Interval q spans p_lo (p_hi/p_lo)^(q/n) ..
- * p_lo (p_hi/p_lo)^((q+1)/n); its trials split it into max(1, ceil(width n_bins / lo)) equal
- * parts (in bins) and take their midpoints, so the last epoch's phase moves by about one bin
- * between neighbouring trials; trials below 1 bin or above n_bins are skipped, and a curve
- * with bin width <= 0 scores 0. d_scores: device FP32 [B][n_intervals]. Asynchronous on the
- * context's stream. Errors: CETRA_EINVAL (bad sizes, p_lo <= 0, p_hi <= p_lo). */
-int cetra_cnn_comb(cetra_ctx *ctx, const float *d_prob, int B, int n_bins,
-                   const double *d_bin_days, double p_lo, double p_hi, int n_intervals,
-                   float *d_scores);
+ * of B per-bin maps d_map [B][n_bins]. Curve b has V_b = d_n_valid[b] valid bins (device
+ * int32 [B]; NULL means n_bins) of d_bin_days[b] days (device FP64 [B]). Interval q spans
+ * p_lo (p_hi/p_lo)^(q/n) .. p_lo (p_hi/p_lo)^((q+1)/n); in bins [blo, bhi), its trials are the
+ * midpoints of max(1, ceil((bhi - blo) V_b / blo)) equal parts (the last epoch's phase moves
+ * by about one bin between neighbouring trials), skipped below 1 bin or above V_b / 2. For a
+ * trial P (F = floor(P 2^32 + 1/2)) and a phase ph < ceil(P), the epochs are
+ * t_e = (ph 2^32 + e F + 2^31) >> 32 < V_b and the score is sum_e map[t_e] / sqrt(E); the
+ * interval's score is the best of those, 0 if none is positive or if the bin width is <= 0.
+ * d_scores: device FP32 [B][n_intervals]. Asynchronous on the context's stream.
+ * Errors: CETRA_EINVAL (NULL pointers, B outside 1..65535, n_bins outside 1..2^30,
+ * n_intervals < 1, p_lo <= 0, p_hi <= p_lo). */
+int cetra_cnn_comb(cetra_ctx *ctx, const float *d_map, int B, int n_bins,
+                   const double *d_bin_days, const int *d_n_valid, double p_lo, double p_hi,
+                   int n_intervals, float *d_scores);
 
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);

@@ -129,14 +129,23 @@ def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return p, m, v
 
 
-def comb(prob, bin_days, p_lo, p_hi, n_intervals):
+def proposal_map(prob, features):
+    """map[b][t] = prob[b][t] sqrt(2 max_j max(features[b][j][t], 0)): the transit probability
+    times the bin's best window SNR (a window's LR is SNR^2 / 2)."""
+    f = np.maximum(np.asarray(features, np.float32).astype(np.float64), 0.0)
+    return np.asarray(prob, np.float32).astype(np.float64) * np.sqrt(2.0 * f.max(axis=1))
+
+
+def comb(prob, bin_days, p_lo, p_hi, n_intervals, n_valid=None):
     """Period comb over per-bin maps prob [B][T] (bin widths bin_days [B] days), plain loops.
 
-    Interval q: edges lo = p_lo (p_hi/p_lo)^(q/n), hi = the same at q + 1, in bins
-    blo = lo / w, bhi = hi / w; trials Pb_m = blo + (bhi - blo)(m + 1/2) / nP with
-    nP = max(1, ceil((bhi - blo) T / blo)), skipped below 1 bin or above T; for each phase
-    ph < ceil(Pb) the epochs t_e = floor(ph + e Pb + 1/2) < T give sum_e p[t_e] / sqrt(E).
-    The interval's score is the largest such value, and 0 if none is positive.
+    Curve b has V = n_valid[b] valid bins (all T when n_valid is None). Interval q: edges
+    lo = p_lo (p_hi/p_lo)^(q/n), hi = the same at q + 1, in bins blo = lo / w, bhi = hi / w;
+    trials Pb_m = blo + (bhi - blo)(m + 1/2) / nP with nP = max(1, ceil((bhi - blo) V / blo)),
+    skipped below 1 bin or above V / 2; with F = floor(Pb 2^32 + 1/2), each phase ph < ceil(Pb)
+    has the epochs t_e = (ph 2^32 + e F + 2^31) >> 32 < V (exact integers) and scores
+    sum_e p[t_e] / sqrt(E). The interval's score is the largest such value, 0 if none is
+    positive.
     """
     import math
     prob = np.asarray(prob, np.float64)
@@ -144,28 +153,31 @@ def comb(prob, bin_days, p_lo, p_hi, n_intervals):
     out = np.zeros((B, n_intervals))
     for b in range(B):
         w = float(bin_days[b])
-        if not w > 0.0:
+        V = T if n_valid is None else min(max(int(n_valid[b]), 0), T)
+        if not w > 0.0 or V == 0:
             continue
         for q in range(n_intervals):
             lo = p_lo * (p_hi / p_lo) ** (q / n_intervals)
             hi = p_lo * (p_hi / p_lo) ** ((q + 1) / n_intervals)
             blo, bhi = lo / w, hi / w
-            nP = max(1, math.ceil((bhi - blo) * T / blo))
+            if bhi < 1.0 or blo > 0.5 * V:
+                continue
+            nP = max(1, math.ceil((bhi - blo) * V / blo))
             best = 0.0
             for m in range(nP):
                 Pb = blo + (bhi - blo) * (m + 0.5) / nP
-                if Pb < 1.0 or Pb > T:
+                if Pb < 1.0 or Pb > 0.5 * V:
                     continue
+                F = math.floor(Pb * 2.0 ** 32 + 0.5)
                 for ph in range(math.ceil(Pb)):
                     idx = []
                     e = 0
                     while True:
-                        t = math.floor(ph + e * Pb + 0.5)
-                        if t >= T:
+                        t = (ph * 2 ** 32 + e * F + 2 ** 31) >> 32
+                        if t >= V:
                             break
                         idx.append(t)
                         e += 1
-                    if idx:
-                        best = max(best, prob[b, idx].sum() / math.sqrt(len(idx)))
+                    best = max(best, prob[b, idx].sum() / math.sqrt(len(idx)))
             out[b, q] = best
     return out

@@ -120,7 +120,8 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_double), _P]),
     "cetra_cnn_adam": (_INT, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float]),
-    "cetra_cnn_comb": (_INT, [_P, _P, _INT, _INT, _P, ctypes.c_double, ctypes.c_double, _INT,
+    "cetra_cnn_map": (_INT, [_P, _P, _P, _INT, _INT, _INT, _P]),
+    "cetra_cnn_comb": (_INT, [_P, _P, _INT, _INT, _P, _P, ctypes.c_double, ctypes.c_double, _INT,
                               _P]),
     "cetra_search_batch": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
                                   _INT, _P, _INT, _P, _P, _P, _P]),

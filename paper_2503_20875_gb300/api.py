@@ -454,8 +454,16 @@ class CNN:
             pass
 
 
-def cetra_cnn_comb(ctx: Context, d_prob, d_bin_days, p_lo, p_hi, n_intervals, d_scores):
-    B, T = d_prob.shape
-    check(N.lib.cetra_cnn_comb(ctx.handle, _ptr(d_prob), int(B), int(T), _ptr(d_bin_days),
-                               float(p_lo), float(p_hi), int(n_intervals), _ptr(d_scores)),
-          ctx.handle, "cnn_comb")
+def cetra_cnn_map(ctx: Context, d_prob, d_features, d_map):
+    """d_map = d_prob * sqrt(2 * max over durations of d_features) (device tensors)."""
+    B, J, T = d_features.shape
+    check(N.lib.cetra_cnn_map(ctx.handle, _ptr(d_prob), _ptr(d_features), int(B), int(J), int(T),
+                              _ptr(d_map)), ctx.handle, "cnn_map")
+
+
+def cetra_cnn_comb(ctx: Context, d_map, d_bin_days, p_lo, p_hi, n_intervals, d_scores,
+                   d_n_valid=None):
+    B, T = d_map.shape
+    check(N.lib.cetra_cnn_comb(ctx.handle, _ptr(d_map), int(B), int(T), _ptr(d_bin_days),
+                               _ptr(d_n_valid), float(p_lo), float(p_hi), int(n_intervals),
+                               _ptr(d_scores)), ctx.handle, "cnn_comb")

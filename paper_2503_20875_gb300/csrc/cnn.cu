@@ -28,6 +28,7 @@ constexpr int CONV_TT = 256;       // time bins per block
 constexpr int CONV_RT = 8;         // time bins per thread
 constexpr int CONV_RC = 8;         // output channels per thread
 constexpr int CONV_THREADS = (CONV_TT / CONV_RT) * (CNN_C / CONV_RC);  // 128
+constexpr size_t kCombSmemMax = 96 * 1024;  // maps up to 24,576 bins are staged in shared memory
 
 // ------------------------------------------------------------------------------- kernels
 
@@ -230,37 +231,62 @@ __global__ void cnn_adam_kernel(float *__restrict__ w, const float *__restrict__
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// Period comb over a per-bin transit map p[b][t] (T bins of bw[b] days). Interval q has
-// log-spaced edges lo = p_lo (p_hi / p_lo)^(q / n_int), hi = the same at q + 1 (days), or
-// blo, bhi in bins. Its trial periods are Pb_m = blo + (bhi - blo)(m + 1/2) / nP,
-// m < nP = max(1, ceil((bhi - blo) T / blo)), so that the phase of the last epoch drifts by at
-// most about one bin between neighbouring trials; periods below 1 bin or above T are skipped.
-// For each trial and phase ph < ceil(Pb) the epochs are t_e = floor(ph + e Pb + 1/2) < T and
-// the score is sum_e p[t_e] / sqrt(E). The interval's score is the best of those (>= 0).
-// One block per (interval, curve); its threads share the (trial, phase) pairs.
+// Proposal map: m[b][t] = p[b][t] sqrt(2 max_j max(f[b][j][t], 0)), the network's transit
+// probability times the best window SNR of the bin (the window LR is SNR^2 / 2, Sec. 2.2).
+__global__ void cnn_map_kernel(const float *__restrict__ prob, const float *__restrict__ f,
+                               int J, int T, int64_t n, float *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const int64_t b = x / T, t = x % T;
+        const float *fb = f + b * J * T + t;
+        float m = 0.0f;
+        for (int j = 0; j < J; ++j) m = fmaxf(m, fb[(int64_t)j * T]);
+        out[x] = prob[x] * sqrtf(2.0f * m);
+    }
+}
+
+// Period comb over per-bin maps p[b][t]: curve b has V = n_valid[b] valid bins of bw[b] days.
+// Interval q has log-spaced edges lo = p_lo (p_hi / p_lo)^(q / n_int), hi = the same at q + 1
+// (days), or blo, bhi in bins. Its trial periods are Pb_m = blo + (bhi - blo)(m + 1/2) / nP,
+// m < nP = max(1, ceil((bhi - blo) V / blo)), so that the phase of the last epoch drifts by at
+// most about one bin between neighbouring trials; trials below 1 bin or above V / 2 are
+// skipped. Epochs run in 32.32 fixed point: F = floor(Pb 2^32 + 1/2), and for each phase
+// ph < ceil(Pb) the epochs are t_e = (ph 2^32 + e F + 2^31) >> 32 < V; the score is
+// sum_e p[t_e] / sqrt(E). The interval's score is the best of those, and 0 if none is positive.
+// One block per (interval, curve); the curve's map is staged in shared memory when it fits,
+// and the block's threads share the (trial, phase) pairs, consecutive lanes taking
+// consecutive phases of one trial.
+template <bool SMEM>
 __global__ void cnn_comb_kernel(const float *__restrict__ p, const double *__restrict__ bw,
-                                int T, double p_lo, double p_hi, int n_int,
-                                float *__restrict__ scores) {
+                                const int *__restrict__ n_valid, int T, double p_lo,
+                                double p_hi, int n_int, float *__restrict__ scores) {
+    extern __shared__ float cmap[];
     const int b = blockIdx.y, q = blockIdx.x;
+    const int V = n_valid ? min(max(n_valid[b], 0), T) : T;
     const float *pb = p + (int64_t)b * T;
+    if (SMEM) {
+        for (int t = threadIdx.x; t < V; t += blockDim.x) cmap[t] = pb[t];
+        __syncthreads();
+    }
+    const float *src = SMEM ? cmap : pb;
     const double lo = p_lo * pow(p_hi / p_lo, (double)q / n_int);
     const double hi = p_lo * pow(p_hi / p_lo, (double)(q + 1) / n_int);
     const double w = bw[b];
     float best = 0.0f;
-    if (w > 0.0) {
-        const double blo = lo / w, bhi = hi / w;  // periods in bins
-        const int64_t nP = max((int64_t)1, (int64_t)ceil((bhi - blo) * (double)T / blo));
-        const int64_t nph = (int64_t)ceil(bhi);  // phases of the longest trial
+    const double blo = w > 0.0 ? lo / w : 0.0, bhi = w > 0.0 ? hi / w : 0.0;  // in bins
+    if (w > 0.0 && V > 0 && bhi >= 1.0 && blo <= 0.5 * (double)V) {
+        const int64_t nP = max((int64_t)1, (int64_t)ceil((bhi - blo) * (double)V / blo));
+        const int64_t nph = (int64_t)ceil(fmin(bhi, 0.5 * (double)V));  // phases of the longest trial
+        const uint64_t end = (uint64_t)V << 32;
         for (int64_t x = threadIdx.x; x < nP * nph; x += blockDim.x) {
             const int64_t m = x / nph, ph = x % nph;
             const double Pb = blo + (bhi - blo) * ((double)m + 0.5) / (double)nP;
-            if (Pb < 1.0 || Pb > (double)T || (double)ph >= ceil(Pb)) continue;
+            if (Pb < 1.0 || Pb > 0.5 * (double)V || (double)ph >= ceil(Pb)) continue;
+            const uint64_t F = (uint64_t)floor(Pb * 4294967296.0 + 0.5);
             float s = 0.0f;
             int E = 0;
-            for (int e = 0;; ++e) {
-                const double te = floor((double)ph + (double)e * Pb + 0.5);
-                if (te >= (double)T) break;
-                s += pb[(int)te];
+            for (uint64_t acc = ((uint64_t)ph << 32) + (1ull << 31); acc < end; acc += F) {
+                s += src[acc >> 32];
                 ++E;
             }
             if (E > 0) best = fmaxf(best, s / sqrtf((float)E));
@@ -272,9 +298,9 @@ __global__ void cnn_comb_kernel(const float *__restrict__ p, const double *__res
     if (lane == 0) red[wid] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float m = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
-        scores[(int64_t)b * n_int + q] = m;
+        float mx = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, red[i]);
+        scores[(int64_t)b * n_int + q] = mx;
     }
 }
 
@@ -534,17 +560,39 @@ int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *n, float lr, float beta1, float be
     return e ? cnn_fail(ctx, e, "cnn_adam") : CETRA_OK;
 }
 
-int cetra_cnn_comb(cetra_ctx *ctx, const float *d_prob, int B, int n_bins,
-                   const double *d_bin_days, double p_lo, double p_hi, int n_intervals,
-                   float *d_scores) {
-    if (!ctx || !d_prob || !d_bin_days || !d_scores || B < 1 || n_bins < 1 || n_intervals < 1 ||
-        !(p_lo > 0.0) || !(p_hi > p_lo))
-        return set_error(ctx, CETRA_EINVAL, "cnn_comb: bad argument");
-    dim3 grid((unsigned)n_intervals, (unsigned)B);
-    cnn_comb_kernel<<<grid, 128, 0, ctx->stream>>>(d_prob, d_bin_days, n_bins, p_lo, p_hi,
-                                                   n_intervals, d_scores);
+int cetra_cnn_map(cetra_ctx *ctx, const float *d_prob, const float *d_features, int B,
+                  int n_dur, int n_bins, float *d_map) {
+    if (!ctx || !d_prob || !d_features || !d_map || B < 1 || n_dur < 1 || n_bins < 1)
+        return set_error(ctx, CETRA_EINVAL, "cnn_map: bad argument");
+    const int64_t n = (int64_t)B * n_bins;
+    cnn_map_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(d_prob, d_features,
+                                                                           n_dur, n_bins, n, d_map);
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
+    return e ? cnn_fail(ctx, e, "cnn_map") : CETRA_OK;
+}
+
+int cetra_cnn_comb(cetra_ctx *ctx, const float *d_prob, int B, int n_bins,
+                   const double *d_bin_days, const int *d_n_valid, double p_lo, double p_hi,
+                   int n_intervals, float *d_scores) {
+    if (!ctx || !d_prob || !d_bin_days || !d_scores || B < 1 || B > 65535 || n_bins < 1 ||
+        n_bins > (1 << 30) || n_intervals < 1 || !(p_lo > 0.0) || !(p_hi > p_lo))
+        return set_error(ctx, CETRA_EINVAL, "cnn_comb: bad argument");
+    dim3 grid((unsigned)n_intervals, (unsigned)B);
+    const size_t smem = (size_t)n_bins * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (smem <= kCombSmemMax) {
+        e = cudaFuncSetAttribute(cnn_comb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (!e)
+            cnn_comb_kernel<true><<<grid, 256, smem, ctx->stream>>>(
+                d_prob, d_bin_days, d_n_valid, n_bins, p_lo, p_hi, n_intervals, d_scores);
+    } else {
+        cnn_comb_kernel<false><<<grid, 256, 0, ctx->stream>>>(
+            d_prob, d_bin_days, d_n_valid, n_bins, p_lo, p_hi, n_intervals, d_scores);
+    }
+    ctx->launches++;
+    if (!e) e = cudaGetLastError();
     return e ? cnn_fail(ctx, e, "cnn_comb") : CETRA_OK;
 }
 

@@ -4,7 +4,8 @@ The periodic search (Sec. 2.3) folds every trial period; this aid picks, per cur
 fraction of log-spaced period intervals to fold instead:
   1. cetra_batch_features: every window's LR (positive depths), max-pooled to
      [durations][n_bins] per curve.
-  2. cetra_cnn_forward: per-bin probability that a bin holds a transit.
+  2. cetra_cnn_forward: per-bin probability that a bin holds a transit; cetra_cnn_map: that
+     probability times the bin's best window SNR.
   3. cetra_cnn_comb: a score for each period interval from that map.
   4. each curve's best intervals -> the fold work items (8-period groups) of their periods
      -> cetra_batch_run_items: the fold over those periods only.
@@ -18,7 +19,7 @@ import math
 
 import numpy as np
 
-from .api import Batch, CNN, Context, batch_period_grid, cetra_cnn_comb
+from .api import Batch, CNN, Context, batch_period_grid, cetra_cnn_comb, cetra_cnn_map
 
 N_BINS = 4096
 N_INTERVALS = 512
@@ -63,6 +64,15 @@ def labels(geo, info, planets_per_curve, n_bins=N_BINS):
                 if lo <= hi:
                     out[idx, lo // width:hi // width + 1] = 1.0
     return out
+
+
+def n_valid(geo, n_bins=N_BINS):
+    """Number of feature bins that hold t0 cells, per curve: ceil(I / ceil(I / n_bins))."""
+    out = []
+    for g in geo:
+        I = g[4]
+        out.append(0 if I <= 0 else -(-I // ((I + n_bins - 1) // n_bins)))
+    return np.array(out, np.int32)
 
 
 def bin_days(geo, info, n_bins=N_BINS):
@@ -151,21 +161,42 @@ def predict(cnn: CNN, d_features, chunk=None):
     return out
 
 
-def interval_scores(ctx: Context, geo, info, d_maps, p_hi, n_intervals=N_INTERVALS):
-    """Comb scores [n_curves][n_intervals] of per-bin maps d_maps (host numpy)."""
+def learned_map(ctx: Context, cnn: CNN, d_features):
+    """Transit probability x best window SNR per bin (torch CUDA tensor [n_curves][n_bins])."""
     import torch
-    bw = torch.as_tensor(bin_days(geo, info, d_maps.shape[1]), device=d_maps.device)
-    scores = torch.empty((d_maps.shape[0], n_intervals), dtype=torch.float32,
-                         device=d_maps.device)
-    cetra_cnn_comb(ctx, d_maps.contiguous(), bw, P_LO, p_hi, n_intervals, scores)
+    prob = predict(cnn, d_features)
+    out = torch.empty_like(prob)
+    cetra_cnn_map(ctx, prob, d_features, out)
+    return out
+
+
+def snr_map(ctx: Context, d_features):
+    """The map without the network: each bin's best window SNR (probability 1 everywhere)."""
+    import torch
+    ones = torch.ones((d_features.shape[0], d_features.shape[2]), dtype=torch.float32,
+                      device=d_features.device)
+    out = torch.empty_like(ones)
+    cetra_cnn_map(ctx, ones, d_features, out)
+    return out
+
+
+def interval_scores(ctx: Context, geo, info, d_map, p_hi, n_intervals=N_INTERVALS):
+    """Comb scores [n_curves][n_intervals] of per-bin maps d_map (host numpy)."""
+    import torch
+    dev = d_map.device
+    T = d_map.shape[1]
+    bw = torch.as_tensor(bin_days(geo, info, T), device=dev)
+    nv = torch.as_tensor(n_valid(geo, T), device=dev)
+    scores = torch.empty((d_map.shape[0], n_intervals), dtype=torch.float32, device=dev)
+    cetra_cnn_comb(ctx, d_map.contiguous(), bw, P_LO, p_hi, n_intervals, scores, nv)
     return scores.cpu().numpy()
 
 
-def propose_and_fold(ctx: Context, batch: Batch, d_maps, p_hi, top_frac=0.05,
+def propose_and_fold(ctx: Context, batch: Batch, d_map, p_hi, top_frac=0.05,
                      n_intervals=N_INTERVALS):
     """Comb the maps, fold each curve's best intervals; returns (best dict, items, n_periods).
     The batch's linear stage must be current (cetra_batch_features ran on it)."""
     geo = geometry(batch)
-    scores = interval_scores(ctx, geo, batch.info, d_maps, p_hi, n_intervals)
+    scores = interval_scores(ctx, geo, batch.info, d_map, p_hi, n_intervals)
     items, n_per = items_from_scores(geo, scores, p_hi, top_frac, n_intervals)
     return batch.run_items(items, linear=False), items, n_per

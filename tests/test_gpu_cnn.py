@@ -114,28 +114,63 @@ def test_adam_steps_match_oracle():
 
 
 def test_comb_matches_oracle():
+    """Comb scores against the plain-loop definition (same FP64 trial periods, exact
+    integer epochs): FP32 sums of at most a few hundred terms in [0, 1]."""
     torch = _torch()
     from paper_2503_20875_gb300 import Context, cetra_cnn_comb
     ctx = Context(0)
     rng = np.random.default_rng(5)
     T, n = 256, 24
-    prob = rng.uniform(size=(4, T)).astype(np.float32) ** 4
+    prob = rng.uniform(size=(5, T)).astype(np.float32) ** 4
     prob[1, 3::37] = 1.0
-    bw = np.array([0.01, 0.02, 0.0, 0.013])
-    scores = torch.empty((4, n), dtype=torch.float32, device="cuda")
-    cetra_cnn_comb(ctx, torch.from_numpy(prob).cuda(), torch.from_numpy(bw).cuda(), 0.3, 1.9, n,
-                   scores)
-    ref = ocnn.comb(prob, bw, 0.3, 1.9, n)
-    np.testing.assert_allclose(scores.cpu().numpy(), ref, rtol=2e-6, atol=1e-7)
-    assert np.all(scores.cpu().numpy()[2] == 0.0)
+    bw = np.array([0.01, 0.02, 0.0, 0.013, 0.011])
+    nv = np.array([256, 200, 256, 97, 0], np.int32)
+    for valid in (None, nv):
+        scores = torch.empty((5, n), dtype=torch.float32, device="cuda")
+        cetra_cnn_comb(ctx, torch.from_numpy(prob).cuda(), torch.from_numpy(bw).cuda(), 0.3, 1.9,
+                       n, scores, None if valid is None else torch.from_numpy(valid).cuda())
+        ref = ocnn.comb(prob, bw, 0.3, 1.9, n, valid)
+        got = scores.cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-7)
+        assert np.all(got[2] == 0.0)
+    assert np.all(got[4] == 0.0)
 
 
-def _batch(n, seed, **kw):
+def test_comb_large_map_from_global_memory():
+    """A map too large for shared memory (32,768 bins) is read from global memory."""
+    torch = _torch()
+    from paper_2503_20875_gb300 import Context, cetra_cnn_comb
+    ctx = Context(0)
+    T = 32768
+    m = np.zeros((1, T), np.float32)
+    m[0, 11::1000] = 1.0  # 33 pulses every 1000 bins
+    scores = torch.empty((1, 8), dtype=torch.float32, device="cuda")
+    cetra_cnn_comb(ctx, torch.from_numpy(m).cuda(), torch.tensor([1.0], dtype=torch.float64,
+                   device="cuda"), 600.0, 1500.0, 8, scores)
+    got = scores.cpu().numpy()[0]
+    q = int(math.floor(8 * math.log(1000.0 / 600.0) / math.log(1500.0 / 600.0)))
+    assert got[q] == pytest.approx(math.sqrt(33.0), rel=1e-6)
+    assert np.argmax(got) == q
+
+
+def test_proposal_map_matches_oracle():
+    torch = _torch()
+    from paper_2503_20875_gb300 import Context, cetra_cnn_map
+    ctx = Context(0)
+    rng = np.random.default_rng(6)
+    f = (rng.normal(size=(3, 5, 300)) * 10).astype(np.float32)
+    p = rng.uniform(size=(3, 300)).astype(np.float32)
+    out = torch.empty((3, 300), dtype=torch.float32, device="cuda")
+    cetra_cnn_map(ctx, torch.from_numpy(p).cuda(), torch.from_numpy(f).cuda(), out)
+    np.testing.assert_allclose(out.cpu().numpy(), ocnn.proposal_map(p, f), rtol=3e-7, atol=0)
+
+
+def _batch(n, seed, ratio=1.003, **kw):
     from paper_2503_20875_gb300 import Context, Batch
     ws = synth.make_batch_workload(n_curves=n, seed=seed, **kw)
     ctx = Context(0)
     b = Batch(ctx, [(w.time, w.flux, w.flux_err) for w in ws], ws[0].durations, ws[0].template,
-              0.5, None, 1.003, cadence=CAD, t0_step=STEP)
+              0.5, None, ratio, cadence=CAD, t0_step=STEP)
     return ctx, b, ws
 
 
@@ -213,33 +248,41 @@ def _recovered(period, planets):
 def test_learned_proposal_gain():
     """Train on injection curves, then fold only each curve's best 5 % of period intervals.
 
-    The trained network's choice must recover clearly more of the injected planets than a
-    random choice of the same size and than the untrained network, within reach of the
-    full search, while folding a small fraction of the trial periods."""
+    The map the comb reads is the trained network's transit probability times each bin's
+    best window SNR. Against the same comb over the SNR alone (the method without the
+    network), over the untrained network's map, and against a random choice of intervals
+    of the same size, the trained map must recover clearly more of the injected planets,
+    close to the full search, while folding a small fraction of the trial periods."""
     torch = _torch()
     from paper_2503_20875_gb300 import CNN, proposal
     n_bins, frac = 4096, 0.05
     # training set: every curve carries a planet
-    ctx, tb, tws = _batch(256, seed=41, max_sectors=2, planet_frac=1.0, snr_range=(6.0, 20.0))
+    ctx, tb, tws = _batch(512, seed=41, max_sectors=3, planet_frac=1.0, snr_range=(6.0, 20.0),
+                          ratio=None)
     d_f = tb.features(n_bins)
     lab = proposal.labels(proposal.geometry(tb), tb.info, [w.planets for w in tws], n_bins)
     d_y = torch.from_numpy(lab).cuda()
     net = CNN(ctx, d_f.shape[1], n_bins=n_bins, max_batch=32, seed=3)
     untrained = CNN(ctx, d_f.shape[1], n_bins=n_bins, max_batch=32, seed=3)
-    hist = proposal.train(net, d_f, d_y, epochs=12, batch_size=32, lr=2e-3, pos_weight=20.0)
-    assert hist[-1] < 0.7 * hist[0]
+    hist = proposal.train(net, d_f, d_y, epochs=20, batch_size=32, lr=2e-3, pos_weight=20.0)
+    assert hist[-1] < 0.85 * hist[0]
     del d_f
-    # evaluation set
-    _, eb, ews = _batch(96, seed=42, max_sectors=2, planet_frac=1.0, snr_range=(6.0, 20.0))
+    # evaluation set (other seeds), the per-curve period grids of the batched form
+    _, eb, ews = _batch(96, seed=42, max_sectors=3, planet_frac=1.0, snr_range=(6.0, 20.0),
+                        ratio=None)
     geo = proposal.geometry(eb)
     p_hi = proposal.period_max(geo)
     full = eb.run()
     e_f = eb.features(n_bins)
+    maps = {"learned": proposal.learned_map(ctx, net, e_f),
+            "snr_only": proposal.snr_map(ctx, e_f),
+            "untrained": proposal.learned_map(ctx, untrained, e_f)}
     res = {}
-    for name, model in (("learned", net), ("untrained", untrained)):
-        best, items, n_per = proposal.propose_and_fold(ctx, eb, proposal.predict(model, e_f),
-                                                       p_hi, frac)
+    for name, m in maps.items():
+        best, items, n_per = proposal.propose_and_fold(ctx, eb, m, p_hi, frac)
         res[name] = (sum(_recovered(p, w.planets) for p, w in zip(best["period"], ews)), n_per)
+        if name == "learned":  # the fold over the chosen periods never beats the full search
+            assert np.all(best["dlogl"] <= full["dlogl"])
     items, n_per = proposal.random_items(geo, p_hi, frac, seed=5)
     best = eb.run_items(items, linear=False)
     res["random"] = (sum(_recovered(p, w.planets) for p, w in zip(best["period"], ews)), n_per)
@@ -248,7 +291,9 @@ def test_learned_proposal_gain():
     print(f"full search {n_full}/{len(ews)}; " + "; ".join(
         f"{k} {v[0]}/{len(ews)} folding {v[1] / total:.3f} of the periods"
         for k, v in res.items()))
-    assert res["learned"][1] <= 0.12 * total
-    assert res["learned"][0] >= res["random"][0] + 0.15 * len(ews)
-    assert res["learned"][0] >= res["untrained"][0]
-    assert res["learned"][0] >= 0.6 * n_full
+    n = len(ews)
+    assert res["learned"][1] <= 0.1 * total
+    assert res["learned"][0] >= res["snr_only"][0] + 0.1 * n
+    assert res["learned"][0] >= res["untrained"][0] + 0.1 * n
+    assert res["learned"][0] >= res["random"][0] + 0.2 * n
+    assert res["learned"][0] >= 0.85 * n_full

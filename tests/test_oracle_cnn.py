@@ -88,7 +88,7 @@ def test_adam_matches_torch():
 
 def test_comb_constant_map_closed_form():
     """A map of ones: every (trial, phase) scores sqrt(E), the largest E at phase 0 of the
-    shortest trial of the interval, E = ceil((T - 1/2) / Pb)."""
+    shortest trial of the interval: E = ceil((T 2^32 - 2^31) / F), F = floor(P 2^32 + 1/2)."""
     import math
     T, w, n = 300, 0.1, 12
     sc = cnn.comb(np.ones((1, T)), [w], 0.5, 12.0, n)
@@ -96,8 +96,30 @@ def test_comb_constant_map_closed_form():
         lo = 0.5 * (12.0 / 0.5) ** (q / n) / w
         hi = 0.5 * (12.0 / 0.5) ** ((q + 1) / n) / w
         nP = max(1, math.ceil((hi - lo) * T / lo))
-        P0 = lo + (hi - lo) * 0.5 / nP
-        assert sc[0, q] == pytest.approx(math.sqrt(math.ceil((T - 0.5) / P0)), rel=1e-12)
+        F = math.floor((lo + (hi - lo) * 0.5 / nP) * 2.0 ** 32 + 0.5)
+        E = -(-(T * 2 ** 32 - 2 ** 31) // F)
+        assert sc[0, q] == pytest.approx(math.sqrt(E), rel=1e-12)
+
+
+def test_comb_valid_span_is_a_truncation():
+    """Bins past a curve's valid span do not count: the scores equal those of the map cut to
+    that span, whatever the bins past it hold."""
+    rng = np.random.default_rng(6)
+    V, T = 180, 256
+    m = rng.uniform(size=(1, T))
+    m[0, V:] = 1e6
+    a = cnn.comb(m, [0.02], 0.05, 2.0, 10, n_valid=[V])
+    b = cnn.comb(m[:, :V], [0.02], 0.05, 2.0, 10)
+    np.testing.assert_array_equal(a, b)
+    assert a.max() < 1e3
+
+
+def test_proposal_map_worked_values():
+    """p = 0.5 with window LRs 4.5, 8 and -1 in one bin: 0.5 sqrt(2 x 8) = 2; zero features
+    give 0."""
+    f = np.array([[[4.5, 0.0], [8.0, 0.0], [-1.0, 0.0]]], np.float32)
+    got = cnn.proposal_map(np.array([[0.5, 0.9]], np.float32), f)
+    np.testing.assert_array_equal(got, [[2.0, 0.0]])
 
 
 def test_comb_finds_planted_pulse_train():

@@ -84,3 +84,15 @@ def test_items_budget_and_empty_curves():
         assert len(full) >= n_keep  # the kept intervals are folded in full
         for x in mine:  # and every kept group serves one of them
             assert np.isin(q[8 * x:8 * x + 8], full).any()
+
+
+def test_n_valid_counts_occupied_bins():
+    geo = [(0.0, 0.5, 1.001, 10, I, 0) for I in (1000, 777, 50, 4097, 1)] + \
+          [(0.0, 0.5, 1.001, 0, 0, 0)]
+    for n_bins in (64, 100, 256, 4096):
+        got = proposal.n_valid(geo, n_bins)
+        for g, v in zip(geo, got):
+            I = g[4]
+            width = max(1, (I + n_bins - 1) // n_bins)
+            assert v == len({i // width for i in range(I)})
+            assert v <= n_bins
