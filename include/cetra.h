@@ -357,6 +357,25 @@ int cetra_batch_curve(const cetra_batch *batch, int curve, double *t_ref, double
                       double *period_ratio, int32_t *n_periods, int32_t *n_t0,
                       int64_t *first_item);
 
+/*
+ * Fold the periods a proposal chose (learned period-interval proposal; not in the paper) and
+ * report each curve's best over them. d_scores: device FP32 [n_curves][n_intervals]
+ * (cetra_cnn_comb's output), interval q spanning [e_q, e_{q+1}) days with
+ * e_q = p_lo (p_hi/p_lo)^(q/n_intervals). Per curve, on the device: of the intervals holding
+ * at least one of its periods (n_present), the max(1, ceil(top_frac n_present)) with the
+ * highest scores are kept (NaN ranks lowest; ties: lower interval first); every 8-period
+ * group holding a period of a kept interval is folded (periods outside [p_lo, p_hi) are never
+ * chosen). linear != 0 reruns the resample and linear stages first. Outputs (host, each may be
+ * NULL): best [n_curves]; *n_items_out = groups folded; *n_periods_out = periods in them;
+ * items_out (capacity n_fold_items) = the folded work items, in no fixed order. Blocks until
+ * done. Errors: CETRA_EINVAL (n_intervals outside 1..1024, p_lo <= 0, p_hi <= p_lo,
+ * top_frac outside (0, 1]), CETRA_ECUDA, CETRA_ETIMEOUT.
+ */
+int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *batch, const float *d_scores,
+                             int n_intervals, double p_lo, double p_hi, double top_frac,
+                             int linear, cetra_best *best, int64_t *n_items_out,
+                             int64_t *n_periods_out, int64_t *items_out);
+
 /* One-shot batched search: cetra_batch_create (no autotuning) + cetra_batch_run +
  * cetra_batch_destroy. */
 int cetra_search_batch(cetra_ctx *ctx, const cetra_params *params, int n_curves,

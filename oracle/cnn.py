@@ -181,3 +181,39 @@ def comb(prob, bin_days, p_lo, p_hi, n_intervals, n_valid=None):
                     best = max(best, prob[b, idx].sum() / math.sqrt(len(idx)))
             out[b, q] = best
     return out
+
+
+def propose_items(curves, scores, p_lo, p_hi, top_frac):
+    """Fold work items a proposal keeps (plain definition).
+
+    curves: per curve (periods, first_item), its trial periods ascending. Interval q spans
+    [e_q, e_{q+1}) with e_q = p_lo (p_hi/p_lo)^(q/n); a period outside [p_lo, p_hi) belongs to
+    none. Of the intervals holding at least one period, the max(1, ceil(top_frac x their
+    number)) with the highest scores are kept (NaN lowest; ties: lower q first); every group
+    of 8 consecutive periods (k // 8) holding a period of a kept interval is an item,
+    numbered first_item + k // 8. Returns (sorted items, number of periods in them).
+    """
+    import math
+    scores = np.asarray(scores, np.float64)
+    n = scores.shape[1]
+    edges = np.array([p_lo * (p_hi / p_lo) ** (q / n) for q in range(n + 1)])
+    items, n_per = [], 0
+    for c, (P, first) in enumerate(curves):
+        P = np.asarray(P, np.float64)
+        K = P.size
+        q = np.searchsorted(edges, P, side="right") - 1
+        inside = (q >= 0) & (q < n)
+        present = sorted(set(q[inside].tolist()))
+        if not present:
+            continue
+        n_keep = max(1, math.ceil(top_frac * len(present)))
+
+        def rank_key(v):
+            s = scores[c, v]
+            return (-(s if s == s else -np.inf), v)
+
+        kept = set(sorted(present, key=rank_key)[:n_keep])
+        groups = sorted({k // 8 for k in range(K) if inside[k] and q[k] in kept})
+        n_per += sum(min(8, K - 8 * g) for g in groups)
+        items += [first + g for g in groups]
+    return np.array(sorted(items), np.int64), n_per

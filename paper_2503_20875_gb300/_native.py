@@ -120,6 +120,8 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_double), _P]),
     "cetra_cnn_adam": (_INT, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float]),
+    "cetra_batch_run_proposed": (_INT, [_P, _P, _P, _INT, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _INT, _P, _P, _P, _P]),
     "cetra_cnn_map": (_INT, [_P, _P, _P, _INT, _INT, _INT, _P]),
     "cetra_cnn_comb": (_INT, [_P, _P, _INT, _INT, _P, _P, ctypes.c_double, ctypes.c_double, _INT,
                               _P]),

@@ -309,10 +309,16 @@ class Batch:
     """cetra_batch_create / run / destroy over a list of (time, flux, flux_err) curves."""
 
     def __init__(self, ctx: Context, curves, durations, tmpl, period_min, period_max=None,
-                 period_ratio=None, autotune=False, **params):
+                 period_ratio=None, autotune=False, csr=None, **params):
+        """curves: a list of (time, flux, flux_err); or csr = (offsets [n + 1], time, flux,
+        flux_err) already packed back to back (then curves is ignored)."""
         self.ctx = ctx
-        off, t, f, e = _pack(curves)
-        n = len(curves)
+        if csr is not None:
+            off = _np(csr[0], np.int64)
+            t, f, e = _np(csr[1], np.float64), _np(csr[2], np.float32), _np(csr[3], np.float32)
+        else:
+            off, t, f, e = _pack(curves)
+        n = off.size - 1
         d = _np(durations, np.float64)
         tm = _np(tmpl, np.float32)
         pmin = _np(np.broadcast_to(period_min, (n,)), np.float64)
@@ -340,12 +346,16 @@ class Batch:
               "batch_run")
         return _best_dict(best) if results else None
 
-    def features(self, n_bins=4096):
-        """Max-pooled linear LR [n_curves][n_dur][n_bins] (torch CUDA tensor)."""
+    def features(self, n_bins=4096, out=None):
+        """Max-pooled linear LR [n_curves][n_dur][n_bins] (torch CUDA tensor; written into
+        `out` when given, a contiguous tensor of that shape)."""
         import torch
         J = self.info["n_dur"]
-        out = torch.empty((self.n, J, n_bins), dtype=torch.float32,
-                          device=torch.device("cuda", self.ctx.device))
+        if out is None:
+            out = torch.empty((self.n, J, n_bins), dtype=torch.float32,
+                              device=torch.device("cuda", self.ctx.device))
+        elif tuple(out.shape) != (self.n, J, n_bins) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous [n_curves][n_dur][n_bins] tensor")
         check(N.lib.cetra_batch_features(self.ctx.handle, self.handle, int(n_bins), _ptr(out)),
               self.ctx.handle, "batch_features")
         return out
@@ -367,6 +377,22 @@ class Batch:
                                           int(bool(linear)), best), self.ctx.handle,
               "batch_run_items")
         return _best_dict(best)
+
+    def run_proposed(self, d_scores, p_lo, p_hi, top_frac, linear=False, items=False):
+        """Fold each curve's best-scored period intervals (selection on the device).
+        Returns (best dict, n_items, n_periods[, items])."""
+        if tuple(d_scores.shape[:1]) != (self.n,) or not d_scores.is_contiguous():
+            raise ValueError("d_scores must be a contiguous [n_curves][n_intervals] tensor")
+        best = (N.cetra_best * self.n)()
+        n_it, n_per = ctypes.c_int64(), ctypes.c_int64()
+        buf = np.empty(max(1, self.info["n_fold_items"]), np.int64) if items else None
+        check(N.lib.cetra_batch_run_proposed(self.ctx.handle, self.handle, _ptr(d_scores),
+                                             int(d_scores.shape[1]), float(p_lo), float(p_hi),
+                                             float(top_frac), int(bool(linear)), best,
+                                             ctypes.byref(n_it), ctypes.byref(n_per), _ptr(buf)),
+              self.ctx.handle, "batch_run_proposed")
+        out = (_best_dict(best), n_it.value, n_per.value)
+        return out + (np.sort(buf[:n_it.value]),) if items else out
 
     def close(self):
         if self.handle:

@@ -41,6 +41,8 @@ struct cetra_batch {
     cetra_best *d_best = nullptr;
     int *d_queue = nullptr, *d_status = nullptr;
     int64_t *d_items = nullptr;  // explicit fold work list (cetra_batch_run_items)
+    unsigned char *d_flags = nullptr;        // one byte per work item (proposal selection)
+    unsigned long long *d_counts = nullptr;  // selected items, their periods
 };
 
 namespace {
@@ -110,9 +112,11 @@ cudaError_t enqueue_linear(cetra_batch *b, int lin_threads) {
                                b->d_curves, b->d_wy, b->d_w, b->d_ab);
 }
 
-// The fold over n_items work items (item_list NULL: items 0 .. n_items-1) and the finalize.
+// The fold over n_items work items (item_list NULL: items 0 .. n_items-1; n_items_dev not
+// NULL: the first *n_items_dev entries of item_list, at most n_items) and the finalize.
 cudaError_t enqueue_fold(cetra_batch *b, int64_t n_items, int fold_variant,
-                         const int64_t *item_list) {
+                         const int64_t *item_list,
+                         const unsigned long long *n_items_dev = nullptr) {
     cetra_plan *plan = b->plan;
     cudaStream_t st = b->stream;
     cudaError_t e;
@@ -121,7 +125,7 @@ cudaError_t enqueue_fold(cetra_batch *b, int64_t n_items, int fold_variant,
     if ((e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st))) return e;  // queue, status
     if ((e = launch_batch_fold(st, b->fold_blocks, fold_variant, plan, b->d_ab, b->d_curves,
                                b->d_group_off, b->n_curves, n_items, b->d_queue, b->d_pkeys,
-                               b->d_keys, b->d_status, item_list)))
+                               b->d_keys, b->d_status, item_list, n_items_dev)))
         return e;
     return launch_batch_finalize(st, plan, b->d_ab, b->d_curves, b->n_curves, b->d_pkeys,
                                  b->d_keys, b->d_status, b->d_best);
@@ -307,7 +311,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     // device memory, one allocation carved in 256-byte aligned pieces
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0, o_time, o_flux, o_err, o_wy, o_w, o_ab, o_pt, o_tile, o_grp, o_cv, o_keys,
-                    o_pkeys, o_best, o_q, o_items;
+                    o_pkeys, o_best, o_q, o_items, o_flags, o_cnt;
     o_time = off; off = up(off + (size_t)n_points * sizeof(double));
     o_flux = off; off = up(off + (size_t)n_points * sizeof(float));
     o_err = off; off = up(off + (size_t)n_points * sizeof(float));
@@ -323,6 +327,8 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_best = off; off = up(off + (size_t)n_curves * sizeof(cetra_best));
     o_q = off; off = up(off + 2 * sizeof(int));
     o_items = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1) * sizeof(int64_t));
+    o_flags = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1));
+    o_cnt = off; off = up(off + 2 * sizeof(unsigned long long));
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e) return bail(cuda_fail(ctx, e, "batch device"));
     e = cudaMalloc(&b->d_mem, off);
@@ -348,6 +354,8 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     b->d_queue = reinterpret_cast<int *>(base + o_q);
     b->d_status = b->d_queue + 1;
     b->d_items = reinterpret_cast<int64_t *>(base + o_items);
+    b->d_flags = reinterpret_cast<unsigned char *>(base + o_flags);
+    b->d_counts = reinterpret_cast<unsigned long long *>(base + o_cnt);
 
     if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) ||
         (e = cudaEventCreate(&b->ev_start)) || (e = cudaEventCreate(&b->ev_stop)))
@@ -450,6 +458,44 @@ int cetra_batch_run_items(cetra_ctx *ctx, cetra_batch *b, const int64_t *items, 
     if (e) return cuda_fail(ctx, e, "batch_run_items");
     ctx->launches += linear ? 4 : 2;
     if (status != 0) return set_error(ctx, CETRA_ETIMEOUT, "batch_run_items: a device wait timed out");
+    return CETRA_OK;
+}
+
+int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *b, const float *d_scores,
+                             int n_intervals, double p_lo, double p_hi, double top_frac,
+                             int linear, cetra_best *best, int64_t *n_items_out,
+                             int64_t *n_periods_out, int64_t *items_out) {
+    if (!ctx || !b || !d_scores || n_intervals < 1 || n_intervals > SEL_MAX_INTERVALS ||
+        !(p_lo > 0.0) || !(p_hi > p_lo) || !std::isfinite(p_hi) || !(top_frac > 0.0) ||
+        !(top_frac <= 1.0))
+        return set_error(ctx, CETRA_EINVAL, "batch_run_proposed: bad argument");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
+    if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
+    if (!e && linear) e = enqueue_linear(b, b->lin_threads);
+    if (!e) e = cudaMemsetAsync(b->d_counts, 0, 2 * sizeof(unsigned long long), b->stream);
+    if (!e)
+        e = launch_batch_select(b->stream, b->d_curves, b->d_group_off, b->n_curves, d_scores,
+                                n_intervals, p_lo, p_hi, top_frac, b->d_flags, b->d_items,
+                                b->d_counts);
+    if (!e) e = enqueue_fold(b, b->n_items, b->fold_variant, b->d_items, b->d_counts);
+    unsigned long long counts[2] = {0, 0};
+    int status = 0;
+    if (!e && best)
+        e = cudaMemcpyAsync(best, b->d_best, (size_t)b->n_curves * sizeof(cetra_best),
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaMemcpyAsync(counts, b->d_counts, sizeof(counts), cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaStreamSynchronize(b->stream);
+    if (!e && items_out && counts[0])
+        e = cudaMemcpy(items_out, b->d_items, (size_t)counts[0] * sizeof(int64_t),
+                       cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(ctx, e, "batch_run_proposed");
+    ctx->launches += linear ? 5 : 3;
+    if (n_items_out) *n_items_out = (int64_t)counts[0];
+    if (n_periods_out) *n_periods_out = (int64_t)counts[1];
+    if (status != 0)
+        return set_error(ctx, CETRA_ETIMEOUT, "batch_run_proposed: a device wait timed out");
     return CETRA_OK;
 }
 

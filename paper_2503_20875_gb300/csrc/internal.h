@@ -156,7 +156,15 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
                               unsigned long long *curve_keys, int *status,
-                              const int64_t *item_list);
+                              const int64_t *item_list,
+                              const unsigned long long *n_items_dev = nullptr);
+// Learned-proposal selection: per curve, the fold work items of its best period intervals
+// (SEL_MAX_INTERVALS intervals at most).
+constexpr int SEL_MAX_INTERVALS = 1024;
+cudaError_t launch_batch_select(cudaStream_t stream, const batch_curve *curves,
+                                const int64_t *group_off, int n_curves, const float *scores,
+                                int n_int, double p_lo, double p_hi, double top_frac,
+                                unsigned char *flags, int64_t *items, unsigned long long *counts);
 cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_plan *plan,
                                   const float2 *ab, const batch_curve *curves, int n_curves,
                                   int n_bins, float *out);

@@ -1003,8 +1003,11 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                   const double *__restrict__ durations, double c, int64_t p, int64_t q,
                   int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
                   unsigned long long *__restrict__ curve_keys, int *__restrict__ status,
-                  const int64_t *__restrict__ item_list) {
+                  const int64_t *__restrict__ item_list,
+                  const unsigned long long *__restrict__ n_items_dev) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the queue length: n_items, or the count a device-side selection left (capped by n_items)
+    if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
     float2 *strips = reinterpret_cast<float2 *>(smem_raw);
     int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);
     __shared__ fold_smem sm;
@@ -1093,6 +1096,102 @@ __global__ void batch_finalize_kernel(const float2 *__restrict__ ab,
     out.i = i;
     out.j = j;
     best[cidx] = out;
+}
+
+// Learned-proposal selection (not in the paper), one block per curve. Interval q < n_int
+// spans [e_q, e_{q+1}) days with e_q = p_lo (p_hi / p_lo)^(q / n_int); kst[q] = the number of
+// the curve's periods below e_q (so interval q holds periods kst[q] .. kst[q+1] - 1). Of the
+// intervals holding at least one period ("present"), the max(1, ceil(top_frac n_present))
+// with the highest scores are kept (NaN ranks lowest; ties: lower q first), and every
+// 8-period group holding a period of a kept interval becomes one fold work item. Items are
+// appended to items[] behind the counter counts[0] (their order across curves is not fixed);
+// counts[1] accumulates the periods of the selected groups. flags: one byte per work item of
+// the batch (scratch).
+constexpr int SEL_THREADS = 256;
+__global__ void __launch_bounds__(SEL_THREADS)
+batch_select_kernel(const batch_curve *__restrict__ curves, const int64_t *__restrict__ group_off,
+                    const float *__restrict__ scores, int n_int, double p_lo, double p_hi,
+                    double top_frac, unsigned char *__restrict__ flags,
+                    int64_t *__restrict__ items, unsigned long long *__restrict__ counts) {
+    __shared__ int64_t kst[SEL_MAX_INTERVALS + 1];
+    __shared__ float sc[SEL_MAX_INTERVALS];
+    __shared__ unsigned char keep[SEL_MAX_INTERVALS];
+    __shared__ int s_present;
+    __shared__ unsigned long long s_base;
+    __shared__ int s_warp[SEL_THREADS / 32];
+    __shared__ unsigned long long s_per[SEL_THREADS / 32];
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const batch_curve cv = curves[c];
+    const int64_t K = cv.n_periods;
+    if (K <= 0) return;  // uniform over the block
+    const double lr = log(cv.ratio);
+    for (int q = tid; q <= n_int; q += SEL_THREADS) {
+        const double edge = p_lo * pow(p_hi / p_lo, (double)q / n_int);
+        const double est = ceil(log(edge / cv.pmin) / lr);
+        int64_t k = !(est > 0.0) ? 0 : (est >= (double)K ? K : (int64_t)est);
+        while (k > 0 && batch_period(cv.pmin, cv.ratio, k - 1) >= edge) --k;
+        while (k < K && batch_period(cv.pmin, cv.ratio, k) < edge) ++k;
+        kst[q] = k;
+    }
+    if (tid == 0) s_present = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int q = tid; q < n_int; q += SEL_THREADS) {
+        const float v = scores[(int64_t)c * n_int + q];
+        sc[q] = v == v ? v : -INFINITY;
+        mine += kst[q + 1] > kst[q];
+    }
+    atomicAdd(&s_present, mine);
+    __syncthreads();
+    const int n_present = s_present;
+    if (n_present == 0) return;  // uniform
+    const int n_keep = max(1, (int)ceil(top_frac * (double)n_present));
+    for (int q = tid; q < n_int; q += SEL_THREADS) {
+        unsigned char k = 0;
+        if (kst[q + 1] > kst[q]) {
+            const float v = sc[q];
+            int rank = 0;
+            for (int r = 0; r < n_int; ++r)
+                rank += (kst[r + 1] > kst[r]) && (sc[r] > v || (sc[r] == v && r < q));
+            k = rank < n_keep;
+        }
+        keep[q] = k;
+    }
+    const int64_t g0 = group_off[c], G = (K + FT_G - 1) / FT_G;
+    for (int64_t g = tid; g < G; g += SEL_THREADS) flags[g0 + g] = 0;
+    __syncthreads();
+    for (int q = 0; q < n_int; ++q) {
+        if (!keep[q]) continue;  // uniform: keep[] is shared
+        const int64_t lo = kst[q] / FT_G, hi = (kst[q + 1] - 1) / FT_G;
+        for (int64_t g = lo + tid; g <= hi; g += SEL_THREADS) flags[g0 + g] = 1;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < G; base += SEL_THREADS) {
+        const int64_t g = base + tid;
+        const bool f = g < G && flags[g0 + g];
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
+        unsigned long long per = f ? (unsigned long long)min((int64_t)FT_G, K - g * FT_G) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) per += __shfl_down_sync(0xFFFFFFFFu, per, o);
+        if (lane == 0) {
+            s_warp[wid] = __popc(bal);
+            s_per[wid] = per;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long tot = 0, ptot = 0;
+            for (int w = 0; w < SEL_THREADS / 32; ++w) {
+                const int n = s_warp[w];
+                s_warp[w] = (int)tot;  // exclusive prefix over warps
+                tot += n;
+                ptot += s_per[w];
+            }
+            s_base = tot ? atomicAdd(&counts[0], tot) : 0ull;
+            if (ptot) atomicAdd(&counts[1], ptot);
+        }
+        __syncthreads();
+        if (f) items[s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u))] = g0 + g;
+        __syncthreads();
+    }
 }
 
 // Linear-search features of every batch curve: the window LR = A^2 / (2B) (Sec. 2.2) of
@@ -1294,7 +1393,7 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
                               unsigned long long *curve_keys, int *status,
-                              const int64_t *item_list) {
+                              const int64_t *item_list, const unsigned long long *n_items_dev) {
     if (n_items <= 0) return cudaSuccess;
     auto kern = batch_fold_kernel<false, FT_R>;
     if (plan->precision == CETRA_FP32_KAHAN)
@@ -1303,7 +1402,7 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
         kern = batch_fold_kernel<false, FT_R / 2>;
     kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
         ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
-        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list);
+        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list, n_items_dev);
     return cudaGetLastError();
 }
 
@@ -1317,6 +1416,18 @@ cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, c
     batch_finalize_kernel<<<(n_curves + threads - 1) / threads, threads, 0, stream>>>(
         ab, curves, n_curves, plan->d_durations, plan->cadence, plan->p, plan->q, plan->n_pad,
         period_keys, curve_keys, status, best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_select(cudaStream_t stream, const batch_curve *curves,
+                                const int64_t *group_off, int n_curves, const float *scores,
+                                int n_int, double p_lo, double p_hi, double top_frac,
+                                unsigned char *flags, int64_t *items,
+                                unsigned long long *counts) {
+    if (n_curves <= 0) return cudaSuccess;
+    batch_select_kernel<<<n_curves, SEL_THREADS, 0, stream>>>(curves, group_off, scores, n_int,
+                                                              p_lo, p_hi, top_frac, flags, items,
+                                                              counts);
     return cudaGetLastError();
 }
 

@@ -7,8 +7,8 @@ fraction of log-spaced period intervals to fold instead:
   2. cetra_cnn_forward: per-bin probability that a bin holds a transit; cetra_cnn_map: that
      probability times the bin's best window SNR.
   3. cetra_cnn_comb: a score for each period interval from that map.
-  4. each curve's best intervals -> the fold work items (8-period groups) of their periods
-     -> cetra_batch_run_items: the fold over those periods only.
+  4. cetra_batch_run_proposed: each curve's best intervals -> the fold work items (8-period
+     groups) of their periods, chosen on the device, and the fold over those periods only.
 The network is trained on injection curves: the labels mark the bins that hold an injected
 transit (its mid-time +- half its duration). Every step of the arithmetic runs in the
 library's kernels; this module only does the bookkeeping on the host.
@@ -19,12 +19,11 @@ import math
 
 import numpy as np
 
-from .api import Batch, CNN, Context, batch_period_grid, cetra_cnn_comb, cetra_cnn_map
+from .api import Batch, CNN, Context, cetra_cnn_comb, cetra_cnn_map
 
 N_BINS = 4096
 N_INTERVALS = 512
 P_LO = 0.5
-GROUP = 8   # periods per fold work item
 
 
 # --------------------------------------------------------------------------- host bookkeeping
@@ -43,26 +42,28 @@ def labels(geo, info, planets_per_curve, n_bins=N_BINS):
     """[n_curves][n_bins] float32: 1 for the bins of each curve's t0 grid that hold an
     injected transit (any t0 within D/2 of a transit mid-time), else 0."""
     out = np.zeros((len(geo), n_bins), np.float32)
+    s = info["t0_step"]
     for idx, (g, planets) in enumerate(zip(geo, planets_per_curve)):
         t_ref, I = g[0], g[4]
-        if I <= 0:
+        if I <= 0 or not planets:
             continue
         width = (I + n_bins - 1) // n_bins
-        s = info["t0_step"]
-        i_last = I - 1
+        t_first = t_ref - info["n_pad"] * info["cadence"]  # time of t0 cell 0
+        t_last = t_first + (I - 1) * s
+        diff = np.zeros(n_bins + 1, np.int64)
         for pl in planets:
             P, t0, D = pl["P"], pl["t0"], pl["D"]
-            # mid-times t0 + n P whose +-D/2 span meets the grid (index 0 .. I - 1)
-            t_first = t_ref - info["n_pad"] * info["cadence"]
-            t_last = t_first + i_last * s
-            n_lo = math.floor((t_first - 0.5 * D - t0) / P)
-            n_hi = math.ceil((t_last + 0.5 * D - t0) / P)
-            for n in range(n_lo, n_hi + 1):
-                ic = t0_index(t0 + n * P, t_ref, info)
-                hw = 0.5 * D / s
-                lo, hi = max(math.ceil(ic - hw), 0), min(math.floor(ic + hw), i_last)
-                if lo <= hi:
-                    out[idx, lo // width:hi // width + 1] = 1.0
+            # mid-times t0 + n P whose +-D/2 span meets the grid (cells 0 .. I - 1)
+            n = np.arange(math.floor((t_first - 0.5 * D - t0) / P),
+                          math.ceil((t_last + 0.5 * D - t0) / P) + 1)
+            ic = t0_index(t0 + n * P, t_ref, info)
+            hw = 0.5 * D / s
+            lo = np.maximum(np.ceil(ic - hw), 0).astype(np.int64)
+            hi = np.minimum(np.floor(ic + hw), I - 1).astype(np.int64)
+            ok = lo <= hi
+            np.add.at(diff, lo[ok] // width, 1)
+            np.add.at(diff, hi[ok] // width + 1, -1)
+        out[idx] = (np.cumsum(diff[:n_bins]) > 0).astype(np.float32)
     return out
 
 
@@ -82,53 +83,10 @@ def bin_days(geo, info, n_bins=N_BINS):
                     np.float64)
 
 
-def interval_edges(p_hi, n_intervals=N_INTERVALS):
-    """Edges (days) of the log-spaced intervals the comb scores."""
-    return P_LO * (p_hi / P_LO) ** (np.arange(n_intervals + 1) / n_intervals)
-
-
-def period_intervals(g, p_hi, n_intervals=N_INTERVALS):
-    """Interval index of each trial period of one curve (geometry g)."""
-    _, pmin, ratio, K, _, _ = g
-    P = batch_period_grid(pmin, ratio, K)
-    q = np.searchsorted(interval_edges(p_hi, n_intervals), P, side="right") - 1
-    return np.clip(q, 0, n_intervals - 1)
-
-
-def items_from_scores(geo, scores, p_hi, top_frac=0.05, n_intervals=N_INTERVALS):
-    """Fold work items of the periods in each curve's best intervals.
-
-    Per curve, of the intervals its period grid reaches, the ceil(top_frac x their number)
-    with the highest scores (ties: lower interval first) are kept; an item is one group of
-    GROUP consecutive periods, kept when any of its periods lies in a kept interval.
-    Returns (items int64, kept-period count)."""
-    items, n_periods = [], 0
-    for c, g in enumerate(geo):
-        K, first = g[3], g[5]
-        if K <= 0:
-            continue
-        q = period_intervals(g, p_hi, n_intervals)
-        present = np.unique(q)
-        n_keep = max(1, int(math.ceil(top_frac * present.size)))
-        keep = present[np.argsort(-np.asarray(scores[c])[present], kind="stable")[:n_keep]]
-        groups = np.unique(np.nonzero(np.isin(q, keep))[0] // GROUP)
-        n_periods += int(sum(min(GROUP, K - GROUP * x) for x in groups))
-        items.append(first + groups)
-    return (np.concatenate(items).astype(np.int64) if items else np.zeros(0, np.int64),
-            n_periods)
-
-
 def period_max(geo):
     """Upper edge for the intervals: just above the longest trial period of the batch."""
     top = [g[1] * g[2] ** (g[3] - 1) for g in geo if g[3] > 0]
     return max(top) * (1.0 + 1e-9) if top else 2.0 * P_LO
-
-
-def random_items(geo, p_hi, top_frac, seed, n_intervals=N_INTERVALS):
-    """The same budget as items_from_scores with intervals drawn uniformly at random."""
-    rng = np.random.default_rng(seed)
-    scores = rng.uniform(size=(len(geo), n_intervals))
-    return items_from_scores(geo, scores, p_hi, top_frac, n_intervals)
 
 
 # --------------------------------------------------------------------------- device steps
@@ -181,7 +139,7 @@ def snr_map(ctx: Context, d_features):
 
 
 def interval_scores(ctx: Context, geo, info, d_map, p_hi, n_intervals=N_INTERVALS):
-    """Comb scores [n_curves][n_intervals] of per-bin maps d_map (host numpy)."""
+    """Comb scores [n_curves][n_intervals] of per-bin maps d_map (torch CUDA tensor)."""
     import torch
     dev = d_map.device
     T = d_map.shape[1]
@@ -189,14 +147,14 @@ def interval_scores(ctx: Context, geo, info, d_map, p_hi, n_intervals=N_INTERVAL
     nv = torch.as_tensor(n_valid(geo, T), device=dev)
     scores = torch.empty((d_map.shape[0], n_intervals), dtype=torch.float32, device=dev)
     cetra_cnn_comb(ctx, d_map.contiguous(), bw, P_LO, p_hi, n_intervals, scores, nv)
-    return scores.cpu().numpy()
+    return scores
 
 
 def propose_and_fold(ctx: Context, batch: Batch, d_map, p_hi, top_frac=0.05,
-                     n_intervals=N_INTERVALS):
-    """Comb the maps, fold each curve's best intervals; returns (best dict, items, n_periods).
-    The batch's linear stage must be current (cetra_batch_features ran on it)."""
-    geo = geometry(batch)
+                     n_intervals=N_INTERVALS, geo=None):
+    """Comb the maps and fold each curve's best intervals (selection on the device).
+    Returns (best dict, n_items, n_periods). The batch's linear stage must be current
+    (cetra_batch_features ran on it)."""
+    geo = geo if geo is not None else geometry(batch)
     scores = interval_scores(ctx, geo, batch.info, d_map, p_hi, n_intervals)
-    items, n_per = items_from_scores(geo, scores, p_hi, top_frac, n_intervals)
-    return batch.run_items(items, linear=False), items, n_per
+    return batch.run_proposed(scores, P_LO, p_hi, top_frac)

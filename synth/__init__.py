@@ -18,7 +18,7 @@ Contents
 """
 from .transit import ld_transit_template, default_template, ld_deficit
 from .lightcurves import (log_grid, inject_transits, make_workload, WORKLOADS, Workload,
-                          make_batch_workload)
+                          make_batch_workload, make_batch_csr)
 
 __all__ = ["ld_transit_template", "default_template", "ld_deficit", "log_grid",
-           "inject_transits", "make_workload", "WORKLOADS", "Workload", "make_batch_workload"]
+           "inject_transits", "make_workload", "WORKLOADS", "Workload", "make_batch_workload", "make_batch_csr"]

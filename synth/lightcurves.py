@@ -178,7 +178,7 @@ def make_workload(name, seed=1, **kw):
 
 
 def make_batch_workload(n_curves=8192, seed=1, max_sectors=13, planet_frac=0.3,
-                        snr_range=(5.0, 20.0), min_sectors=1):
+                        snr_range=(5.0, 20.0), min_sectors=1, with_periods=True):
     """Batch of uneven 30-min curves: S ~ U{1..13} sectors of 27.4 d with 1-d gaps.
 
     Per-curve sigma_c log-uniform 500-5,000 ppm, per-point sigma = sigma_c
@@ -186,7 +186,8 @@ def make_batch_workload(n_curves=8192, seed=1, max_sectors=13, planet_frac=0.3,
     with P log-uniform in [1, min(100, T/2)] d and SNR ~ U(snr_range) (5-20),
     depth = SNR sigma_c / sqrt(n_in).
     Returns a list of Workload (16 log-spaced durations 1-16 h, t0 step 10 min,
-    periods log-spaced from 0.5 d to T/2 with ratio 1 + D_min / (2 T)).
+    periods log-spaced from 0.5 d to T/2 with ratio 1 + D_min / (2 T); an empty period
+    array when with_periods is False).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     cad = 1800.0 / DAY_S
@@ -215,8 +216,21 @@ def make_batch_workload(n_curves=8192, seed=1, max_sectors=13, planet_frac=0.3,
                                 rp=0.03))
         noise = rng.normal(size=t.size) * sig
         ratio = 1.0 + durations[0] / (2.0 * T)
-        n_p = int(np.floor(np.log((T / 2.0) / 0.5) / np.log(ratio))) + 1
+        n_p = int(np.floor(np.log((T / 2.0) / 0.5) / np.log(ratio))) + 1 if with_periods else 0
         periods = 0.5 * ratio ** np.arange(n_p)
         out.append(_finish(f"batch_{c}", t, inject_transits(t, planets), noise, sig, durations,
                            periods, cad, 600.0 / DAY_S, planets, "batch member"))
     return out
+
+
+def make_batch_csr(job):
+    """make_batch_workload packed back to back: job = (n_curves, seed, planet_frac).
+    Returns (offsets int64 [n + 1], time f64, flux f32, flux_err f32, planets per curve);
+    a top-level function so that process pools can call it."""
+    n, seed, planet_frac = job
+    ws = make_batch_workload(n_curves=n, seed=seed, planet_frac=planet_frac,
+                             with_periods=False)
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([w.time.size for w in ws])
+    return (off, np.concatenate([w.time for w in ws]), np.concatenate([w.flux for w in ws]),
+            np.concatenate([w.flux_err for w in ws]), [w.planets for w in ws])

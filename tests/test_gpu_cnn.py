@@ -238,6 +238,46 @@ def test_run_items_matches_oracle_on_the_chosen_periods():
         np.testing.assert_array_equal(all_items[key], full[key])
 
 
+def test_run_proposed_matches_oracle_selection():
+    """The device-side choice of work items equals the plain definition in oracle/cnn.py on
+    the same scores (exact integers), and its fold equals folding those items."""
+    torch = _torch()
+    ctx, b, ws = _batch(6, seed=33, max_sectors=3, ratio=None)
+    b.features(512)  # resample + linear stage
+    geo = [b.curve(c) for c in range(b.n)]
+    curves = []
+    for g, w in zip(geo, ws):
+        T = w.time.max() - w.time.min()
+        P = oracle.period_grid(g[1], g[2], 0.5 * T)
+        assert P.size == g[3]
+        curves.append((P, g[5]))
+    p_hi = max(P[-1] for P, _ in curves) * 1.001
+    rng = np.random.default_rng(8)
+    for n_int, frac in ((512, 0.05), (64, 0.3), (1024, 0.01), (16, 1.0)):
+        sc = rng.uniform(size=(b.n, n_int)).astype(np.float32)
+        sc[0, :5] = np.nan
+        sc[1, :] = 0.5  # all tied: the lowest intervals win
+        best, n_it, n_per, items = b.run_proposed(torch.from_numpy(sc).cuda(), 0.5, p_hi, frac,
+                                                  items=True)
+        ref, ref_per = ocnn.propose_items(curves, sc, 0.5, p_hi, frac)
+        np.testing.assert_array_equal(items, ref)
+        assert n_it == ref.size and n_per == ref_per
+        again = b.run_items(items, linear=False)
+        for key in ("k", "i", "j", "dlogl"):
+            np.testing.assert_array_equal(best[key], again[key])
+    # a narrow proposal range: periods outside [p_lo, p_hi) are never folded
+    sc = np.ones((b.n, 8), np.float32)
+    _, _, n_per, items = b.run_proposed(torch.from_numpy(sc).cuda(), 2.0, 3.0, 1.0, items=True)
+    ref, ref_per = ocnn.propose_items(curves, sc, 2.0, 3.0, 1.0)
+    np.testing.assert_array_equal(items, ref)
+    assert n_per == ref_per
+    from paper_2503_20875_gb300 import CetraError
+    with pytest.raises(CetraError):
+        b.run_proposed(torch.from_numpy(sc).cuda(), 2.0, 1.0, 0.5)
+    with pytest.raises(CetraError):
+        b.run_proposed(torch.from_numpy(sc).cuda(), 0.5, 3.0, 0.0)
+
+
 def _recovered(period, planets):
     if not planets or not np.isfinite(period):
         return False
@@ -279,12 +319,12 @@ def test_learned_proposal_gain():
             "untrained": proposal.learned_map(ctx, untrained, e_f)}
     res = {}
     for name, m in maps.items():
-        best, items, n_per = proposal.propose_and_fold(ctx, eb, m, p_hi, frac)
+        best, n_it, n_per = proposal.propose_and_fold(ctx, eb, m, p_hi, frac, geo=geo)
         res[name] = (sum(_recovered(p, w.planets) for p, w in zip(best["period"], ews)), n_per)
         if name == "learned":  # the fold over the chosen periods never beats the full search
             assert np.all(best["dlogl"] <= full["dlogl"])
-    items, n_per = proposal.random_items(geo, p_hi, frac, seed=5)
-    best = eb.run_items(items, linear=False)
+    rnd = torch.rand((eb.n, proposal.N_INTERVALS), generator=torch.Generator().manual_seed(5))
+    best, _, n_per = eb.run_proposed(rnd.cuda(), proposal.P_LO, p_hi, frac)
     res["random"] = (sum(_recovered(p, w.planets) for p, w in zip(best["period"], ews)), n_per)
     n_full = sum(_recovered(p, w.planets) for p, w in zip(full["period"], ews))
     total = sum(g[3] for g in geo)

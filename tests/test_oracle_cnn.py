@@ -143,3 +143,34 @@ def test_comb_finds_planted_pulse_train():
 def test_comb_null_curve_scores_zero():
     sc = cnn.comb(np.ones((2, 64)), [0.0, -1.0], 0.5, 5.0, 4)
     assert np.all(sc == 0.0)
+
+
+def test_propose_items_worked_example():
+    """Periods 1.0, 1.1, ..., 2.9 (20, first item 7), intervals [1, 1.5), [1.5, 2.25),
+    [2.25, 3.375) (p_lo 1, p_hi 3.375, n = 3): periods 0-4 | 5-12 | 13-19. With scores
+    (0.2, 0.9, 0.5) and top_frac 0.34, ceil(1.02) = 2 intervals are kept: 1 and 2, i.e.
+    periods 5-19, groups 0-2 -> items 7, 8, 9 holding all 20 periods."""
+    P = 1.0 + 0.1 * np.arange(20)
+    items, n_per = cnn.propose_items([(P, 7)], [[0.2, 0.9, 0.5]], 1.0, 3.375, 0.34)
+    np.testing.assert_array_equal(items, [7, 8, 9])
+    assert n_per == 20
+    # keep one interval: the middle one (periods 5-12) -> groups 0 (k 5-7) and 1 (k 8-12)
+    items, n_per = cnn.propose_items([(P, 7)], [[0.2, 0.9, 0.5]], 1.0, 3.375, 0.2)
+    np.testing.assert_array_equal(items, [7, 8])
+    assert n_per == 16
+    # a NaN score ranks lowest; equal scores go to the lower interval
+    items, _ = cnn.propose_items([(P, 0)], [[np.nan, 0.5, 0.5]], 1.0, 3.375, 0.2)
+    np.testing.assert_array_equal(items, [0, 1])  # interval 1 (k 5-12)
+
+
+def test_propose_items_everything_and_outside_periods():
+    """top_frac = 1 keeps every group holding a period in [p_lo, p_hi); periods outside are
+    never chosen; a curve without periods gives nothing."""
+    P = np.exp(np.linspace(np.log(0.3), np.log(40.0), 300))
+    rng = np.random.default_rng(9)
+    sc = rng.uniform(size=(2, 16))
+    items, n_per = cnn.propose_items([(P, 0), (np.zeros(0), 38)], sc, 0.5, 20.0, 1.0)
+    ok = np.nonzero((P >= 0.5) & (P < 20.0))[0]
+    want = np.unique(ok // 8)
+    np.testing.assert_array_equal(items, want)
+    assert n_per == sum(min(8, 300 - 8 * g) for g in want)

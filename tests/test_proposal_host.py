@@ -1,5 +1,5 @@
 """Host bookkeeping of the learned period-interval proposal (no GPU): transit labels on the
-t0 grid, interval membership of trial periods, and the fold work items a score table keeps."""
+t0 grid, bin widths, valid spans and the upper interval edge."""
 import math
 
 import numpy as np
@@ -42,48 +42,6 @@ def test_bin_days_and_period_max():
     pmax = proposal.period_max(geo)
     assert pmax >= max(batch_period_grid(0.5, 1.001, 100)[-1], batch_period_grid(0.7, 1.01, 3)[-1])
     assert pmax <= 0.7 * 1.01 ** 2 * (1 + 1e-8)
-
-
-def test_items_keep_the_best_intervals():
-    K, first = 1000, 40
-    geo = [(0.0, 0.5, 1.003, K, 5000, first)]
-    p_hi = proposal.period_max(geo)
-    n_int = 64
-    q = proposal.period_intervals(geo[0], p_hi, n_int)
-    P = batch_period_grid(0.5, 1.003, K)
-    edges = proposal.interval_edges(p_hi, n_int)
-    assert np.all(edges[q] <= P) and np.all(P < edges[q + 1])
-    present = np.unique(q)
-    scores = np.zeros((1, n_int))
-    scores[0, present[5]] = 3.0
-    scores[0, present[-1]] = 2.0
-    scores[0, present[0]] = 1.0
-    items, n_per = proposal.items_from_scores(geo, scores, p_hi, top_frac=2.5 / present.size,
-                                              n_intervals=n_int)
-    want = np.unique(np.nonzero(np.isin(q, present[[5, -1, 0]]))[0] // 8) + first
-    np.testing.assert_array_equal(items, want)
-    assert n_per == sum(min(8, K - 8 * (x - first)) for x in want)
-    assert items.min() >= first and items.max() < first + math.ceil(K / 8)
-
-
-def test_items_budget_and_empty_curves():
-    geo = [(0.0, 0.5, 1.001, 3000, 4000, 0), (0.0, 0.5, 1.001, 0, 0, 375),
-           (0.0, 0.6, 1.002, 700, 4000, 375)]
-    p_hi = proposal.period_max(geo)
-    items, n_per = proposal.random_items(geo, p_hi, 0.05, seed=1)
-    assert np.all(np.diff(items) > 0)  # sorted, unique
-    for g in (geo[0], geo[2]):
-        K, first = g[3], g[5]
-        q = proposal.period_intervals(g, p_hi)
-        n_keep = math.ceil(0.05 * np.unique(q).size)
-        mine = items[(items >= first) & (items < first + math.ceil(K / 8))] - first
-        covered = np.zeros(K, bool)
-        for x in mine:
-            covered[8 * x:8 * x + 8] = True
-        full = [v for v in np.unique(q) if covered[q == v].all()]
-        assert len(full) >= n_keep  # the kept intervals are folded in full
-        for x in mine:  # and every kept group serves one of them
-            assert np.isin(q[8 * x:8 * x + 8], full).any()
 
 
 def test_n_valid_counts_occupied_bins():
