@@ -342,14 +342,24 @@ def run_proposal(args):
     labels = torch.empty((n_train, n_bins), dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
     pos, n_planets, n_points = 0, 0, 0
+    split = {"wait_s": 0.0, "create_s": 0.0, "features_s": 0.0, "labels_s": 0.0}
+    tw = time.perf_counter()
     for off, t, f, e, planets in gen:
+        ta = time.perf_counter()
+        split["wait_s"] += ta - tw
         n = off.size - 1
         b = cetra.Batch(ctx, None, durs, tmpl, 0.5, None, None, csr=(off, t, f, e), cadence=cad,
                         t0_step=step)
+        tb = time.perf_counter()
         b.features(n_bins, out=feats[pos:pos + n])
+        tc = time.perf_counter()
         geo = proposal.geometry(b)
         labels[pos:pos + n] = torch.from_numpy(proposal.labels(geo, b.info, planets, n_bins))
         b.close()
+        tw = time.perf_counter()
+        split["create_s"] += tb - ta
+        split["features_s"] += tc - tb
+        split["labels_s"] += tw - tc
         pos += n
         n_planets += sum(1 for p in planets if p)
         n_points += int(off[-1])
@@ -414,7 +424,7 @@ def run_proposal(args):
                                "random": per_r / total},
             "train": {"curves": n_train, "with_planet": n_planets, "points": n_points,
                       "epochs": args.proposal_epochs, "loss": [round(h, 5) for h in hist],
-                      "data_s": t_data, "train_s": t_train,
+                      "data_s": t_data, "data_split": split, "train_s": t_train,
                       "resident_bytes": n_train * (J + 1) * n_bins * 4}}
     print(json.dumps(line))
 

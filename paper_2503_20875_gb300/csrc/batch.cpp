@@ -81,17 +81,17 @@ int64_t build_tiles(cetra_batch *b, int threads) {
 
 // Algorithmic (A, B) reads of the fold of one curve: about I reads per (period, duration
 // D < P) (each t0 cell belongs to one (phase, epoch) of a period, up to the rounding of
-// the epoch offsets at the ends).
+// the epoch offsets at the ends), over the periods of at least one t0 step. The periods
+// ascend, so per duration the periods above it are a suffix of the grid: O(J) per curve.
 int64_t fold_reads(const cetra_plan *plan, const batch_curve &cv) {
+    const int64_t K = cv.n_periods;
+    if (K <= 0 || cv.I <= 0) return 0;
+    const double s = plan->cadence * (double)plan->p / (double)plan->q;  // t0 step, days
+    const int64_t below_step = period_count(cv.pmin, cv.ratio, std::nextafter(s, 0.0));
     int64_t total = 0;
-    std::vector<double> d(plan->durations);
-    std::sort(d.begin(), d.end());
-    for (int64_t k = 0; k < cv.n_periods; ++k) {
-        const double P = batch_period_host(cv.pmin, cv.ratio, k);
-        const double Ps = (P * (double)plan->q) / (plan->cadence * (double)plan->p);
-        if (!(Ps >= 1.0)) continue;
-        const int64_t nd = std::lower_bound(d.begin(), d.end(), P) - d.begin();
-        total += (int64_t)cv.I * nd;
+    for (double D : plan->durations) {
+        const int64_t upto = std::max(period_count(cv.pmin, cv.ratio, D), below_step);
+        total += (int64_t)cv.I * std::max<int64_t>(0, K - std::min(K, upto));
     }
     return total;
 }
