@@ -83,6 +83,12 @@ def _load():
                                        ctypes.c_int64, P]
     lib.oracle_period_grid.restype = ctypes.c_int64
     lib.oracle_logl0.restype = ctypes.c_double
+    lib.oracle_mask_transits.argtypes = [ctypes.POINTER(_Geom), P, P, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double]
+    lib.oracle_mask_transits.restype = ctypes.c_int64
+    lib.oracle_monotransits.argtypes = [ctypes.POINTER(_Geom), P, ctypes.c_int, P, P,
+                                        ctypes.c_int, P, P]
+    lib.oracle_monotransits.restype = ctypes.c_int
     lib.oracle_num_threads.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -255,3 +261,60 @@ def search(time, flux, flux_err, durations, tmpl, periods=None, *, cadence=0.0, 
     if periods is not None:
         res["periodic"] = periodic(g, durations, lin[0], lin[1], lin[2], periods, mask)
     return res
+
+
+def mask_transits(geom: Geometry, y_grid, w_grid, period, t0, half_width):
+    """R13: copies of (y, w) with the cells within half_width days of any mid-time
+    t0 + n period nulled, and the number of non-null cells that were nulled."""
+    lib = _load()
+    y = np.array(y_grid, np.float64, copy=True)
+    w = np.array(w_grid, np.float64, copy=True)
+    n = lib.oracle_mask_transits(ctypes.byref(geom._raw), _ptr(y), _ptr(w), float(period),
+                                 float(t0), float(half_width))
+    return y, w, int(n)
+
+
+def monotransits(geom: Geometry, durations, depth, lr, max_events):
+    """R14: (i, j) of up to max_events single-transit events, strongest first."""
+    lib = _load()
+    d = np.ascontiguousarray(durations, np.float64)
+    dep = np.ascontiguousarray(depth, np.float64)
+    l = np.ascontiguousarray(lr, np.float64)
+    ii = np.empty(max(1, max_events), np.int64)
+    jj = np.empty(max(1, max_events), np.int32)
+    n = lib.oracle_monotransits(ctypes.byref(geom._raw), _ptr(d), d.size, _ptr(dep), _ptr(l),
+                                int(max_events), _ptr(ii), _ptr(jj))
+    if n < 0:
+        raise MemoryError("oracle monotransits")
+    return ii[:n].copy(), jj[:n].copy()
+
+
+def t0_of(geom: Geometry, i):
+    """Mid-time of t0 index i: t_ref + (i p - n_pad q) c / q."""
+    return geom.t_ref + ((float(i * geom.p - geom.n_pad * geom.q)) * geom.cadence) / float(geom.q)
+
+
+def search_iterative(time, flux, flux_err, durations, tmpl, periods, n_iter, width=2.0, *,
+                     cadence=0.0, t0_step=0.0, L=1024, mask=None):
+    """Sec. 4.2 with R13: search, null the cells within width/2 durations of the best
+    signal's mid-times, search again; n_iter detections (fewer if a search finds nothing).
+    Each detection: dict(k, period, t0, duration, depth, depth_var, dlogl, i, j)."""
+    g = geometry(time, flux, flux_err, durations, cadence, t0_step)
+    y, w = resample(time, flux, flux_err, g)
+    T = template(tmpl, L)
+    P = np.ascontiguousarray(periods, np.float64)
+    out = []
+    for r in range(n_iter):
+        dep, var, lr = linear(g, y, w, durations, T)
+        per = periodic(g, durations, dep, var, lr, P, mask)
+        if np.all(np.isnan(per["dlogl"])):
+            break
+        k = int(np.nanargmax(per["dlogl"]))
+        det = dict(k=k, period=float(P[k]), t0=float(per["t0"][k]),
+                   duration=float(per["duration"][k]), depth=float(per["depth"][k]),
+                   depth_var=float(per["depth_var"][k]), dlogl=float(per["dlogl"][k]),
+                   i=int(per["i"][k]), j=int(per["j"][k]), lr=per["dlogl"], linear=(dep, var, lr))
+        out.append(det)
+        if r + 1 < n_iter:
+            y, w, _ = mask_transits(g, y, w, det["period"], det["t0"], 0.5 * width * det["duration"])
+    return out, g

@@ -41,6 +41,17 @@
  *   R12 A period shorter than one t0 step (P/s < 1) has no distinct phase and
  *       would fold one window onto itself; such a period (and a non-finite
  *       one) is null.
+ *   R13 Masking a detected signal (Sec. 4.2: before each new search the flux in
+ *       and around the previous search's best signal is nulled) acts on
+ *       the resampled grid: cell k, at g_k = t_ref + (k - n_pad) c, is nulled
+ *       when |g_k - (t0 + n P)| < h for the nearest epoch n = floor(d/P + 1/2),
+ *       d = g_k - t0; h is half the masked width (a multiple of the duration,
+ *       chosen by the caller).
+ *   R14 Single-transit (monotransit) events from the linear search (Sec. 1,
+ *       Sec. 5): greedily, the window with the largest LR among windows with a
+ *       positive depth whose mid-time is not within an earlier event's
+ *       duration of that event's mid-time (|i - i_e| < D_e q / (c p), FP64);
+ *       ties go to the smallest j, then the smallest i.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (R8 needs
  * -ffp-contract=off: aarch64 compilers contract a*b+c into fma by default).
@@ -476,4 +487,65 @@ double oracle_logl0(const oracle_geom *g, const double *y_grid, const double *w_
         s += -0.5 * y_grid[k] * y_grid[k] * w_grid[k] - 0.5 * log(2.0 * M_PI / w_grid[k]);
     }
     return s;
+}
+
+/*
+ * R13: null the resampled cells within h (days) of any mid-time t0 + n P of a
+ * detected signal: W_k = 0 and y_k = 0 (the cell then carries no information).
+ * Returns the number of cells nulled by this call.
+ */
+int64_t oracle_mask_transits(const oracle_geom *g, double *y_grid, double *w_grid, double P,
+                             double t0, double h) {
+    int64_t n_masked = 0;
+    if (!(P > 0.0) || !isfinite(P) || !(h > 0.0)) return 0;
+    for (int64_t k = 0; k < g->n_grid; k++) {
+        double gk = g->t_ref + (double)(k - g->n_pad) * g->cadence;
+        double d = gk - t0;
+        double n = floor(d / P + 0.5);
+        double r = fabs(d - n * P);
+        if (r < h) {
+            if (w_grid[k] > 0.0) n_masked++;
+            w_grid[k] = 0.0;
+            y_grid[k] = 0.0;
+        }
+    }
+    return n_masked;
+}
+
+/*
+ * R14: up to max_events single-transit events from the linear-search arrays
+ * ([J][I] depth and LR; NaN marks a null window). Writes each event's (i, j) and
+ * returns how many were found.
+ */
+int oracle_monotransits(const oracle_geom *g, const double *durations, int n_dur,
+                        const double *depth, const double *lr, int max_events,
+                        int64_t *ev_i, int32_t *ev_j) {
+    const int64_t I = g->n_t0;
+    double *half = (double *)malloc(sizeof(double) * (size_t)(max_events > 0 ? max_events : 1));
+    if (!half) return -1;
+    int n = 0;
+    for (; n < max_events; n++) {
+        double best = 0.0;
+        int64_t bi = -1;
+        int bj = -1;
+        for (int j = 0; j < n_dur; j++) {
+            for (int64_t i = 0; i < I; i++) {
+                double v = lr[(int64_t)j * I + i];
+                if (isnan(v) || !(depth[(int64_t)j * I + i] > 0.0)) continue;
+                int hidden = 0;
+                for (int e = 0; e < n && !hidden; e++)
+                    hidden = (double)llabs(i - ev_i[e]) < half[e];
+                if (hidden) continue;
+                if (bj < 0 || v > best) {  /* first in (j, i) order wins ties */
+                    best = v; bi = i; bj = j;
+                }
+            }
+        }
+        if (bj < 0) break;
+        ev_i[n] = bi;
+        ev_j[n] = bj;
+        half[n] = (durations[bj] * (double)g->q) / (g->cadence * (double)g->p);
+    }
+    free(half);
+    return n;
 }
