@@ -439,6 +439,76 @@ int cetra_cnn_comb(cetra_ctx *ctx, const float *d_map, int B, int n_bins,
                    const double *d_bin_days, const int *d_n_valid, double p_lo, double p_hi,
                    int n_intervals, float *d_scores);
 
+/* ---------------------------------------------------------------------------------------
+ * Method neighbours of the search.
+ *
+ * Masking (Sec. 4.2: before each further search of a curve, the flux in and around the best
+ * signal of the previous search is nulled). The mask acts on the resampled grid: cell k, at
+ * time g_k = t_ref + (k - n_pad) c, is nulled (W y = W = 0) when |g_k - (t0 + n P)| < h for
+ * its nearest epoch n = floor((g_k - t0) / P + 1/2), evaluated in FP64 with one rounding per
+ * operation. h is half the masked width (days).
+ *
+ * Single-transit (monotransit) events (Sec. 1 and Sec. 5: single transits are searched for
+ * in the linear-search output): greedily, the window (i, j) with the largest LR among the
+ * windows with a positive depth whose t0 index is not hidden by an earlier event e, hidden
+ * meaning |i - i_e| < D_{j_e} q / (c p) (FP64: the event's duration in t0 steps); ties go to
+ * the smallest j, then the smallest i.
+ * ------------------------------------------------------------------------------------- */
+#define CETRA_MAX_EVENTS 4096
+
+typedef struct {
+    double dlogl;      /* the window's LR, A^2 / (2B), from its FP32 sums in FP64 */
+    double t0;         /* mid-time, absolute days */
+    double duration;   /* days */
+    double depth;      /* A / B */
+    double depth_var;  /* 1 / B */
+    int64_t i;         /* t0 index */
+    int32_t j;         /* duration index */
+    int32_t pad_;
+} cetra_event;
+
+/* Device path: null the cells of the resampled grid in `d_workspace` (from
+ * cetra_resample_device) within half_width days of the mid-times t0 + n period. Rerun
+ * cetra_linear_device afterwards. d_n_masked (device, may be NULL) is increased by the number
+ * of nulled cells that held data. half_width = 0 does nothing. Asynchronous.
+ * Errors: CETRA_EINVAL (period <= 0 or not finite, t0 not finite, half_width < 0),
+ * CETRA_ECAPACITY (workspace smaller than cetra_workspace_bytes(plan, 0)). */
+int cetra_mask_transits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                               size_t workspace_bytes, double period, double t0,
+                               double half_width, unsigned long long *d_n_masked);
+
+/* Host path: mask a grid from cetra_linear_search (as above) and rerun its linear stage, so
+ * that the next cetra_periodic_search / cetra_monotransit_search sees the masked curve.
+ * *n_masked (may be NULL) = nulled cells that held data. Blocks until done. */
+int cetra_mask_transits(cetra_ctx *ctx, cetra_linear_grid *grid, double period, double t0,
+                        double half_width, int64_t *n_masked);
+
+/* Bytes of workspace cetra_monotransits_device needs (>= cetra_workspace_bytes(plan, 0)). */
+size_t cetra_monotransit_workspace_bytes(const cetra_plan *plan, int max_events);
+
+/* Device path: up to max_events single-transit events (strongest first) from the linear grid
+ * in d_workspace (cetra_linear_device), into d_events (device, max_events) and *d_n_events
+ * (device int). Asynchronous. Errors: CETRA_EINVAL (max_events outside 1..4096),
+ * CETRA_ECAPACITY (workspace below cetra_monotransit_workspace_bytes; n_t0 > 2^24 or more
+ * than 256 durations). */
+int cetra_monotransits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                              size_t workspace_bytes, int max_events, cetra_event *d_events,
+                              int *d_n_events);
+
+/* Host path: the same on a grid from cetra_linear_search; events (host, max_events) and
+ * *n_events filled. Blocks until done. */
+int cetra_monotransit_search(cetra_ctx *ctx, cetra_linear_grid *grid, int max_events,
+                             cetra_event *events, int *n_events);
+
+/* Iterative search (Sec. 4.2): n_iter rounds of cetra_periodic_search on the grid, each round
+ * after the first on the curve with the previous round's best signal masked over
+ * width x its duration (width <= 0: 2, i.e. within one duration of each mid-time). out
+ * (host, n_iter) gets each round's best model (k its period index, j its duration index,
+ * i = -1); *n_found = rounds that found a model. The grid is left masked. Blocks. */
+int cetra_search_iterative(cetra_ctx *ctx, cetra_linear_grid *grid, const double *periods,
+                           int n_periods, const uint8_t *dur_mask, int n_iter, double width,
+                           cetra_best *out, int *n_found);
+
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);
 

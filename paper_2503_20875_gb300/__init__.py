@@ -7,11 +7,15 @@ Importing this package loads that library and fails loudly if it is absent.
 from .api import (Context, Plan, DeviceSearch, LinearGrid, Batch, make_params,
                   cetra_linear_search, cetra_periodic_search, cetra_resample_device,
                   cetra_linear_device, cetra_periodic_device, cetra_logl0_device,
-                  cetra_search_batch, CNN, cetra_cnn_map, cetra_cnn_comb)
+                  cetra_search_batch, CNN, cetra_cnn_map, cetra_cnn_comb,
+                  cetra_mask_transits, cetra_monotransit_search, cetra_search_iterative,
+                  cetra_mask_transits_device, cetra_monotransits_device)
 from ._native import CetraError, LIB_PATH
 
 __all__ = ["Context", "Plan", "DeviceSearch", "LinearGrid", "Batch", "cetra_search_batch",
-           "CNN", "cetra_cnn_map", "cetra_cnn_comb",
+           "CNN", "cetra_cnn_map", "cetra_cnn_comb", "cetra_mask_transits",
+           "cetra_monotransit_search", "cetra_search_iterative", "cetra_mask_transits_device",
+           "cetra_monotransits_device",
            "make_params", "cetra_linear_search",
            "cetra_periodic_search", "cetra_resample_device", "cetra_linear_device",
            "cetra_periodic_device", "cetra_logl0_device", "CetraError", "LIB_PATH"]

@@ -47,6 +47,13 @@ class cetra_best(ctypes.Structure):
                 ("j", ctypes.c_int32), ("n_periods", ctypes.c_int32)]
 
 
+class cetra_event(ctypes.Structure):
+    _fields_ = [("dlogl", ctypes.c_double), ("t0", ctypes.c_double),
+                ("duration", ctypes.c_double), ("depth", ctypes.c_double),
+                ("depth_var", ctypes.c_double), ("i", ctypes.c_int64), ("j", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
 class cetra_batch_info(ctypes.Structure):
     _fields_ = [("n_curves", ctypes.c_int32), ("n_dur", ctypes.c_int32),
                 ("n_points", ctypes.c_int64), ("n_cells", ctypes.c_int64),
@@ -101,6 +108,15 @@ SIGNATURES = {
                                    ctypes.POINTER(_I64)]),
     "cetra_periodic_search": (_INT, [_P, _P, _P, _INT, _P, _P, _P, _P, _P, _P,
                                      ctypes.POINTER(_I64)]),
+    "cetra_mask_transits_device": (_INT, [_P, _P, _P, _SZ, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _P]),
+    "cetra_mask_transits": (_INT, [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(_I64)]),
+    "cetra_monotransit_workspace_bytes": (_SZ, [_P, _INT]),
+    "cetra_monotransits_device": (_INT, [_P, _P, _P, _SZ, _INT, _P, _P]),
+    "cetra_monotransit_search": (_INT, [_P, _P, _INT, _P, ctypes.POINTER(_INT)]),
+    "cetra_search_iterative": (_INT, [_P, _P, _P, _INT, _P, _INT, ctypes.c_double, _P,
+                                      ctypes.POINTER(_INT)]),
     "cetra_grid_free": (None, [_P]),
     "cetra_batch_create": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
                                   _INT, _P, _INT, _P, _P, _P, _INT, ctypes.POINTER(_P)]),

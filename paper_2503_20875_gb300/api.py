@@ -203,6 +203,31 @@ class DeviceSearch:
         return self
 
 
+def cetra_mask_transits_device(ctx: Context, plan: Plan, d_workspace, period, t0, half_width,
+                               d_n_masked=None):
+    """Null the resampled cells within half_width days of t0 + n period (then rerun
+    cetra_linear_device)."""
+    check(N.lib.cetra_mask_transits_device(ctx.handle, plan.handle, _ptr(d_workspace),
+                                           d_workspace.numel() * d_workspace.element_size(),
+                                           float(period), float(t0), float(half_width),
+                                           _ptr(d_n_masked)), ctx.handle, "mask_transits_device")
+
+
+def cetra_monotransits_device(ctx: Context, plan: Plan, d_workspace, max_events, d_events, d_n):
+    """Single-transit events into d_events (a device byte tensor of max_events records)
+    and d_n (device int32)."""
+    check(N.lib.cetra_monotransits_device(ctx.handle, plan.handle, _ptr(d_workspace),
+                                          d_workspace.numel() * d_workspace.element_size(),
+                                          int(max_events), _ptr(d_events), _ptr(d_n)),
+          ctx.handle, "monotransits_device")
+
+
+def events_dict(events):
+    """Records of cetra_event -> dict of numpy arrays."""
+    return {f: np.array([getattr(e, f) for e in events])
+            for f, _ in N.cetra_event._fields_ if f != "pad_"}
+
+
 # ----------------------------------------------------------------------------- host-buffer path
 
 class LinearGrid:
@@ -254,6 +279,38 @@ def cetra_linear_search(ctx: Context, time, flux, flux_err, durations, tmpl, *, 
                                     _ptr(var), _ptr(lr), ctypes.byref(n_t0)),
           ctx.handle, "linear_search")
     return (LinearGrid(ctx, grid) if keep_grid else None), depth, var, lr
+
+
+def cetra_mask_transits(ctx: Context, grid: LinearGrid, period, t0, half_width) -> int:
+    """Mask a grid around t0 + n period (half_width days) and rerun its linear stage;
+    returns the number of nulled cells that held data."""
+    n = ctypes.c_int64(0)
+    check(N.lib.cetra_mask_transits(ctx.handle, grid.handle, float(period), float(t0),
+                                    float(half_width), ctypes.byref(n)), ctx.handle,
+          "mask_transits")
+    return n.value
+
+
+def cetra_monotransit_search(ctx: Context, grid: LinearGrid, max_events=10) -> dict:
+    """Up to max_events single-transit events of a grid, strongest first."""
+    ev = (N.cetra_event * int(max_events))()
+    n = ctypes.c_int(0)
+    check(N.lib.cetra_monotransit_search(ctx.handle, grid.handle, int(max_events), ev,
+                                         ctypes.byref(n)), ctx.handle, "monotransit_search")
+    return events_dict(list(ev)[:n.value])
+
+
+def cetra_search_iterative(ctx: Context, grid: LinearGrid, periods, n_iter=3, width=2.0,
+                           mask=None) -> dict:
+    """n_iter rounds of the periodic search, masking each round's best signal (Sec. 4.2)."""
+    P = _np(periods, np.float64)
+    m = None if mask is None else _np(mask, np.uint8)
+    out = (N.cetra_best * int(n_iter))()
+    n = ctypes.c_int(0)
+    check(N.lib.cetra_search_iterative(ctx.handle, grid.handle, _ptr(P), P.size, _ptr(m),
+                                       int(n_iter), float(width), out, ctypes.byref(n)),
+          ctx.handle, "search_iterative")
+    return _best_dict(list(out)[:n.value])
 
 
 def cetra_periodic_search(ctx: Context, grid: LinearGrid, periods, mask=None) -> dict:

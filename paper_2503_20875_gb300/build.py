@@ -25,7 +25,8 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu"]
+SOURCES = ["kernels.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu",
+           "neighbours.cu"]
 
 
 def _cmd(src: str, obj: str) -> list[str]:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -424,6 +425,26 @@ int cetra_linear_search(cetra_ctx *ctx, const cetra_params *params, const double
     return CETRA_OK;
 }
 
+namespace {
+// Enlarge a grid's workspace to `total` bytes, keeping its contents.
+int grow_workspace(cetra_ctx *ctx, cetra_linear_grid *grid, size_t total) {
+    if (grid->work_bytes >= total) return CETRA_OK;
+    void *bigger = nullptr;
+    cudaError_t e = cudaMalloc(&bigger, total);
+    if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "workspace allocation");
+    e = cudaMemcpyAsync(bigger, grid->d_work, grid->work_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(bigger);
+        return cuda_fail(ctx, e, "workspace copy");
+    }
+    cudaFree(grid->d_work);
+    grid->d_work = bigger;
+    grid->work_bytes = total;
+    return CETRA_OK;
+}
+}  // namespace
+
 int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double *periods,
                           int n_periods, const uint8_t *dur_mask, double *dlogl, double *t0,
                           double *duration, double *depth, double *depth_var, int64_t *best_k) {
@@ -438,21 +459,8 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
     cetra_plan *plan = grid->plan;
     device_guard g(ctx->device);
     // the grid workspace is sized without keys; periodic needs a larger one
-    ws_layout L = workspace_layout(plan, n_periods);
-    if (grid->work_bytes < L.total) {
-        void *bigger = nullptr;
-        cudaError_t e = cudaMalloc(&bigger, L.total);
-        if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "periodic_search: workspace allocation");
-        e = cudaMemcpyAsync(bigger, grid->d_work, grid->work_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) {
-            cudaFree(bigger);
-            return cuda_fail(ctx, e, "periodic_search: workspace copy");
-        }
-        cudaFree(grid->d_work);
-        grid->d_work = bigger;
-        grid->work_bytes = L.total;
-    }
+    int rc0 = grow_workspace(ctx, grid, workspace_layout(plan, n_periods).total);
+    if (rc0 != CETRA_OK) return rc0;
     const size_t K = (size_t)n_periods, J = (size_t)plan->J;
     const size_t bytes = K * sizeof(double) * 6 + K * J + 256;
     char *d_buf = nullptr;
@@ -496,6 +504,148 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
                 bk = (int64_t)k;
             }
         *best_k = bk;
+    }
+    return CETRA_OK;
+}
+
+// ------------------------------------------------------------------ method neighbours
+
+int cetra_mask_transits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                               size_t workspace_bytes, double period, double t0,
+                               double half_width, unsigned long long *d_n_masked) {
+    if (!ctx || !plan || !d_workspace) return set_error(ctx, CETRA_EINVAL, "mask: NULL argument");
+    if (!(period > 0.0) || !std::isfinite(period) || !std::isfinite(t0) ||
+        !(half_width >= 0.0) || !std::isfinite(half_width))
+        return set_error(ctx, CETRA_EINVAL, "mask: period must be > 0, t0 and half_width finite, half_width >= 0");
+    ws_layout L = workspace_layout(plan, 0);
+    if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "mask: workspace too small");
+    if (half_width == 0.0) return CETRA_OK;
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = launch_mask(ctx, plan, w.wy, w.w, period, t0, half_width, d_n_masked);
+    return e != cudaSuccess ? cuda_fail(ctx, e, "mask launch") : CETRA_OK;
+}
+
+int cetra_mask_transits(cetra_ctx *ctx, cetra_linear_grid *grid, double period, double t0,
+                        double half_width, int64_t *n_masked) {
+    if (!ctx || !grid || !grid->plan) return set_error(ctx, CETRA_EINVAL, "mask_transits: NULL grid");
+    device_guard g(ctx->device);
+    unsigned long long *d_n = nullptr;
+    cudaError_t e = cudaMalloc((void **)&d_n, sizeof(unsigned long long));
+    if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "mask_transits: allocation");
+    unsigned long long n = 0;
+    e = cudaMemsetAsync(d_n, 0, sizeof(n), ctx->stream);
+    int rc = e != cudaSuccess ? cuda_fail(ctx, e, "mask_transits") : CETRA_OK;
+    if (rc == CETRA_OK)
+        rc = cetra_mask_transits_device(ctx, grid->plan, grid->d_work, grid->work_bytes, period, t0,
+                                        half_width, d_n);
+    if (rc == CETRA_OK)  // the linear stage again, on the masked grid
+        rc = cetra_linear_device(ctx, grid->plan, grid->d_work, grid->work_bytes, nullptr, nullptr,
+                                 nullptr);
+    if (rc == CETRA_OK) {
+        e = cudaMemcpyAsync(&n, d_n, sizeof(n), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "mask_transits");
+    }
+    cudaFree(d_n);
+    if (rc == CETRA_OK && n_masked) *n_masked = (int64_t)n;
+    return rc;
+}
+
+int cetra_monotransits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,
+                              size_t workspace_bytes, int max_events, cetra_event *d_events,
+                              int *d_n_events) {
+    if (!ctx || !plan || !d_workspace || !d_events || !d_n_events)
+        return set_error(ctx, CETRA_EINVAL, "monotransits: NULL argument");
+    if (max_events < 1 || max_events > CETRA_MAX_EVENTS)
+        return set_error(ctx, CETRA_EINVAL, "monotransits: max_events outside 1..4096");
+    if (plan->n_t0 > 0x1000000 || plan->J > 256)
+        return set_error(ctx, CETRA_ECAPACITY, "monotransits: needs n_t0 <= 2^24 and n_dur <= 256");
+    ws_layout L = workspace_layout(plan, (int)mono_scratch_words(plan, max_events));
+    if (workspace_bytes < L.total)
+        return set_error(ctx, CETRA_ECAPACITY, "monotransits: workspace too small");
+    device_guard g(ctx->device);
+    ws_ptrs w = carve(d_workspace, L);
+    cudaError_t e = launch_monotransits(ctx, plan, w.ab, w.keys, max_events, d_events, d_n_events);
+    return e != cudaSuccess ? cuda_fail(ctx, e, "monotransits launch") : CETRA_OK;
+}
+
+size_t cetra_monotransit_workspace_bytes(const cetra_plan *plan, int max_events) {
+    if (!plan || max_events < 1) return 0;
+    return workspace_layout(plan, (int)mono_scratch_words(plan, max_events)).total;
+}
+
+int cetra_monotransit_search(cetra_ctx *ctx, cetra_linear_grid *grid, int max_events,
+                             cetra_event *events, int *n_events) {
+    if (!ctx || !grid || !grid->plan || !events || !n_events)
+        return set_error(ctx, CETRA_EINVAL, "monotransit_search: NULL argument");
+    if (max_events < 1 || max_events > CETRA_MAX_EVENTS)
+        return set_error(ctx, CETRA_EINVAL, "monotransit_search: max_events outside 1..4096");
+    *n_events = 0;
+    device_guard g(ctx->device);
+    int rc = grow_workspace(ctx, grid, cetra_monotransit_workspace_bytes(grid->plan, max_events));
+    if (rc != CETRA_OK) return rc;
+    char *d_buf = nullptr;
+    const size_t ev_bytes = (size_t)max_events * sizeof(cetra_event);
+    cudaError_t e = cudaMalloc((void **)&d_buf, ev_bytes + 256);
+    if (e != cudaSuccess) return set_error(ctx, CETRA_ENOMEM, "monotransit_search: allocation");
+    cetra_event *d_ev = reinterpret_cast<cetra_event *>(d_buf);
+    int *d_n = reinterpret_cast<int *>(d_buf + ev_bytes);
+    rc = cetra_monotransits_device(ctx, grid->plan, grid->d_work, grid->work_bytes, max_events,
+                                   d_ev, d_n);
+    int n = 0;
+    if (rc == CETRA_OK) {
+        e = cudaMemcpyAsync(&n, d_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(events, d_ev, ev_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "monotransit_search");
+    }
+    cudaFree(d_buf);
+    if (rc == CETRA_OK) *n_events = n;
+    return rc;
+}
+
+int cetra_search_iterative(cetra_ctx *ctx, cetra_linear_grid *grid, const double *periods,
+                           int n_periods, const uint8_t *dur_mask, int n_iter, double width,
+                           cetra_best *out, int *n_found) {
+    if (!ctx || !grid || !grid->plan || !out || !n_found)
+        return set_error(ctx, CETRA_EINVAL, "search_iterative: NULL argument");
+    if (n_iter < 1 || n_periods < 1 || !periods)
+        return set_error(ctx, CETRA_EINVAL, "search_iterative: need n_iter >= 1 and periods");
+    if (!(width > 0.0)) width = 2.0;
+    if (!std::isfinite(width)) return set_error(ctx, CETRA_EINVAL, "search_iterative: width not finite");
+    *n_found = 0;
+    const size_t K = (size_t)n_periods;
+    std::vector<double> lr(K), t0(K), dur(K), dep(K), var(K);
+    for (int r = 0; r < n_iter; ++r) {
+        int64_t bk = -1;
+        int rc = cetra_periodic_search(ctx, grid, periods, n_periods, dur_mask, lr.data(),
+                                       t0.data(), dur.data(), dep.data(), var.data(), &bk);
+        if (rc != CETRA_OK) return rc;
+        if (bk < 0) break;
+        cetra_best b{};
+        b.dlogl = lr[bk];
+        b.period = periods[bk];
+        b.t0 = t0[bk];
+        b.duration = dur[bk];
+        b.depth = dep[bk];
+        b.depth_var = var[bk];
+        b.k = bk;
+        b.i = -1;
+        b.j = -1;
+        for (int j = 0; j < grid->plan->J; ++j)
+            if (grid->plan->durations[j] == b.duration) {
+                b.j = j;
+                break;
+            }
+        b.n_periods = n_periods;
+        out[r] = b;
+        *n_found = r + 1;
+        if (r + 1 < n_iter) {
+            rc = cetra_mask_transits(ctx, grid, b.period, b.t0, 0.5 * width * b.duration, nullptr);
+            if (rc != CETRA_OK) return rc;
+        }
     }
     return CETRA_OK;
 }

@@ -158,6 +158,13 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               unsigned long long *curve_keys, int *status,
                               const int64_t *item_list,
                               const unsigned long long *n_items_dev = nullptr);
+// Method neighbours (neighbours.cu): masking a detected signal, single-transit events.
+cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float *wy, float *w, double P,
+                        double t0, double h, unsigned long long *counts);
+size_t mono_scratch_words(const cetra_plan *plan, int max_events);
+cudaError_t launch_monotransits(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
+                                unsigned long long *scratch, int max_events,
+                                cetra_event *events, int *n_events);
 // Learned-proposal selection: per curve, the fold work items of its best period intervals
 // (SEL_MAX_INTERVALS intervals at most).
 constexpr int SEL_MAX_INTERVALS = 1024;
