@@ -264,7 +264,7 @@ def search(time, flux, flux_err, durations, tmpl, periods=None, *, cadence=0.0, 
 
 
 def mask_transits(geom: Geometry, y_grid, w_grid, period, t0, half_width):
-    """R13: copies of (y, w) with the cells within half_width days of any mid-time
+    """R17: copies of (y, w) with the cells within half_width days of any mid-time
     t0 + n period nulled, and the number of non-null cells that were nulled."""
     lib = _load()
     y = np.array(y_grid, np.float64, copy=True)
@@ -275,7 +275,7 @@ def mask_transits(geom: Geometry, y_grid, w_grid, period, t0, half_width):
 
 
 def monotransits(geom: Geometry, durations, depth, lr, max_events):
-    """R14: (i, j) of up to max_events single-transit events, strongest first."""
+    """R18: (i, j) of up to max_events single-transit events, strongest first."""
     lib = _load()
     d = np.ascontiguousarray(durations, np.float64)
     dep = np.ascontiguousarray(depth, np.float64)
@@ -296,7 +296,7 @@ def t0_of(geom: Geometry, i):
 
 def search_iterative(time, flux, flux_err, durations, tmpl, periods, n_iter, width=2.0, *,
                      cadence=0.0, t0_step=0.0, L=1024, mask=None):
-    """Sec. 4.2 with R13: search, null the cells within width/2 durations of the best
+    """Sec. 4.2 with R17: search, null the cells within width/2 durations of the best
     signal's mid-times, search again; n_iter detections (fewer if a search finds nothing).
     Each detection: dict(k, period, t0, duration, depth, depth_var, dlogl, i, j)."""
     g = geometry(time, flux, flux_err, durations, cadence, t0_step)

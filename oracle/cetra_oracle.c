@@ -41,13 +41,13 @@
  *   R12 A period shorter than one t0 step (P/s < 1) has no distinct phase and
  *       would fold one window onto itself; such a period (and a non-finite
  *       one) is null.
- *   R13 Masking a detected signal (Sec. 4.2: before each new search the flux in
+ *   R17 Masking a detected signal (Sec. 4.2: before each new search the flux in
  *       and around the previous search's best signal is nulled) acts on
  *       the resampled grid: cell k, at g_k = t_ref + (k - n_pad) c, is nulled
  *       when |g_k - (t0 + n P)| < h for the nearest epoch n = floor(d/P + 1/2),
  *       d = g_k - t0; h is half the masked width (a multiple of the duration,
  *       chosen by the caller).
- *   R14 Single-transit (monotransit) events from the linear search (Sec. 1,
+ *   R18 Single-transit (monotransit) events from the linear search (Sec. 1,
  *       Sec. 5): greedily, the window with the largest LR among windows with a
  *       positive depth whose mid-time is not within an earlier event's
  *       duration of that event's mid-time (|i - i_e| < D_e q / (c p), FP64);
@@ -490,7 +490,7 @@ double oracle_logl0(const oracle_geom *g, const double *y_grid, const double *w_
 }
 
 /*
- * R13: null the resampled cells within h (days) of any mid-time t0 + n P of a
+ * R17: null the resampled cells within h (days) of any mid-time t0 + n P of a
  * detected signal: W_k = 0 and y_k = 0 (the cell then carries no information).
  * Returns the number of cells nulled by this call.
  */
@@ -513,7 +513,7 @@ int64_t oracle_mask_transits(const oracle_geom *g, double *y_grid, double *w_gri
 }
 
 /*
- * R14: up to max_events single-transit events from the linear-search arrays
+ * R18: up to max_events single-transit events from the linear-search arrays
  * ([J][I] depth and LR; NaN marks a null window). Writes each event's (i, j) and
  * returns how many were found.
  */

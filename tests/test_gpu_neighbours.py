@@ -1,5 +1,5 @@
 """Method neighbours on the GPU against the oracle: masking a detected signal and the
-iterative search (Sec. 4.2, reading R13), single-transit events (Sec. 1, Sec. 5, reading R14)."""
+iterative search (Sec. 4.2, reading R17), single-transit events (Sec. 1, Sec. 5, reading R18)."""
 import ctypes
 
 import numpy as np

@@ -1,5 +1,5 @@
 """Pins of the oracle's method-neighbour steps: masking a detected signal (Sec. 4.2, reading
-R13) and single-transit events from the linear search (Sec. 1, Sec. 5, reading R14)."""
+R17) and single-transit events from the linear search (Sec. 1, Sec. 5, reading R18)."""
 from fractions import Fraction
 import math
 
