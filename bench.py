@@ -389,16 +389,28 @@ def run_proposal(args):
     t_full = time.perf_counter() - t2
 
     def proposed(make_map):
+        """features -> map -> comb -> selection + fold; wall time of each stage (each ends
+        in a synchronisation)."""
+        split = {}
         torch.cuda.synchronize(dev)
         ta = time.perf_counter()
-        d_f = eb.features(n_bins)
+        d_f = eb.features(n_bins)  # resample + linear + max-pool (blocks)
+        tb = time.perf_counter()
         m = make_map(d_f)
-        best, n_it, n_per = proposal.propose_and_fold(ctx, eb, m, p_hi, args.proposal_frac, geo=geo)
-        return best, n_per, time.perf_counter() - ta
+        torch.cuda.synchronize(dev)
+        tc = time.perf_counter()
+        scores = proposal.interval_scores(ctx, geo, eb.info, m, p_hi)
+        torch.cuda.synchronize(dev)
+        td = time.perf_counter()
+        best, n_it, n_per = eb.run_proposed(scores, proposal.P_LO, p_hi, args.proposal_frac)
+        te = time.perf_counter()
+        split = {"features_ms": 1e3 * (tb - ta), "map_ms": 1e3 * (tc - tb),
+                 "comb_ms": 1e3 * (td - tc), "select_fold_ms": 1e3 * (te - td)}
+        return best, n_per, te - ta, split
 
     proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))  # warm-up
-    best_l, per_l, t_prop = proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))
-    best_s, per_s, _ = proposed(lambda d_f: proposal.snr_map(ctx, d_f))
+    best_l, per_l, t_prop, split_l = proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))
+    best_s, per_s, _, _ = proposed(lambda d_f: proposal.snr_map(ctx, d_f))
     rnd = torch.rand((eb.n, proposal.N_INTERVALS), generator=torch.Generator().manual_seed(5))
     best_r, _, per_r = eb.run_proposed(rnd.to(dev), proposal.P_LO, p_hi, args.proposal_frac)
     n_inj = sum(1 for p in planets if p)
@@ -416,6 +428,7 @@ def run_proposal(args):
                        "intervals": proposal.N_INTERVALS, "top_frac": args.proposal_frac,
                        "n_periods": int(total)},
             "full_search": {"value": n_eval / t_full, "unit": UNIT, "ms": 1e3 * t_full},
+            "proposal_split": split_l,
             "speedup": t_full / t_prop,
             "recall": {"criterion": "1 % of P, P/2 or 2P", "injected": n_inj,
                        "full": rec(full), "learned": rec(best_l), "snr_only": rec(best_s),
