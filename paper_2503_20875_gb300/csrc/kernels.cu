@@ -270,6 +270,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                  : "memory");
 }
+// Arrive on a barrier (release: the thread's earlier shared-memory reads are done).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -330,7 +334,8 @@ constexpr int32_t FT_SENT = INT32_MAX;  // epoch past the end of the t0 grid
 
 // Shared state of the fold block.
 struct fold_smem {
-    uint64_t bar[FT_NSTAGE];
+    uint64_t bar[FT_NSTAGE];    // stage filled (bulk copy landed)
+    uint64_t empty[FT_NSTAGE];  // stage drained (every warp done reading it)
     unsigned long long red[FT_THREADS / 32];
     unsigned long long best[FT_G][FT_THREADS];
     double P[FT_G], Ps[FT_G];
@@ -341,7 +346,10 @@ struct fold_smem {
 };
 
 // Ring of bulk copies: `n` counts copies issued (thread 0) or consumed (all threads);
-// copy n lands in stage n % FT_NSTAGE, completing that stage's barrier phase n / FT_NSTAGE.
+// copy n lands in stage n % FT_NSTAGE, completing phase n / FT_NSTAGE of that stage's `bar`.
+// Every warp arrives on the stage's `empty` barrier once it has read the stage, and thread 0
+// waits for that phase before the stage takes copy n + FT_NSTAGE, so warps run up to
+// FT_NSTAGE - 1 epochs apart instead of meeting at a block barrier every epoch.
 struct ring {
     uint32_t n = 0, stage = 0, parity = 0;
     __device__ void next() {
@@ -425,7 +433,11 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
             }
             // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
             auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
+            bool ok = true;
+            // (thread 0) copy epoch e's strip once every warp has drained the stage
             auto issue = [&](int e) {
+                if (iss.n >= FT_NSTAGE && !mbar_wait(&sm.empty[iss.stage], iss.parity ^ 1u))
+                    return false;
                 const int a = (i0 + tmin[e]) & ~1;
                 const int len = ((i0 + tmin[e] + tlen[e] + T - a) + 1) & ~1;
                 const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
@@ -433,12 +445,31 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                 mbar_expect_tx(&sm.bar[iss.stage], bytes);
                 bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
                 iss.next();
+                return true;
             };
-            if (t == 0)
-                for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
-            for (int e = 0; live(e); ++e) {
-                if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
-                const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
+            // every decision that ends the loop is uniform within a warp (the warp's lanes
+            // meet in __syncwarp below): warp 0 learns thread 0's issue outcome by shuffle,
+            // and a warp stops if any of its lanes' waits ran out
+            if (t < 32) {
+                bool iok = true;
+                if (t == 0)
+                    for (int e = 0; iok && e < FT_NSTAGE - 1 && live(e); ++e) iok = issue(e);
+                ok = __shfl_sync(0xFFFFFFFFu, iok, 0);
+            }
+            for (int e = 0; ok && live(e); ++e) {
+                if (t < 32) {
+                    bool iok = true;
+                    if (t == 0 && live(e + FT_NSTAGE - 1)) iok = issue(e + FT_NSTAGE - 1);
+                    if (!__shfl_sync(0xFFFFFFFFu, iok, 0)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&sm.bar[con.stage], con.parity))) {
+                    ok = false;
+                    break;
+                }
+                const int stage = con.stage;
                 const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
                 con.next();
                 const int32_t *de = d + e * GS;
@@ -477,32 +508,35 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                         }
                     }
                 }
-                if (__syncthreads_or(!ok)) {
-                    // a copy did not land in time: record it, drain the ring, stop
-                    if (t == 0) {
-                        atomicExch(status, CETRA_ETIMEOUT);
-                        while (con.n < iss.n) {
-                            mbar_wait(&sm.bar[con.stage], con.parity);
-                            con.next();
-                        }
-                    }
-                    return false;
-                }
+                __syncwarp();
+                if ((t & 31) == 0) mbar_arrive(&sm.empty[stage]);
             }
-            // LR = SA^2 / (2 SB) per (period, phase); the running max keeps the first
-            // (smallest j, then smallest i) of equal values
+            if (__syncthreads_or(!ok)) {
+                // a wait ran out: record it, drain the copies in flight, stop
+                if (t == 0) {
+                    atomicExch(status, CETRA_ETIMEOUT);
+                    while (con.n < iss.n) {
+                        mbar_wait(&sm.bar[con.stage], con.parity);
+                        con.next();
+                    }
+                }
+                return false;
+            }
+            // 2 LR = SA^2 / SB per (period, phase) (a null sum gives NaN, never a maximum);
+            // the running max keeps the first (smallest j, then smallest i) of equal values
 #pragma unroll
             for (int gg = 0; gg < GS; ++gg) {
                 if (!((use >> gg) & 1u)) continue;
                 const int nph = sm.nph[g0 + gg];
+                const bool whole = i0 + T <= nph;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int i = i0 + t + r * FT_THREADS;
                     float2 v = acc[gg][r];
                     if constexpr (KAHAN) add2(v, cmp[gg][r]);
-                    const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
-                    if (i < nph && v.y > 0.0f && lr > best_lr[gg]) {
-                        best_lr[gg] = lr;
+                    const float lr2 = v.x * __fdividef(v.x, v.y);
+                    if ((whole || i < nph) && lr2 > best_lr[gg]) {
+                        best_lr[gg] = lr2;
                         best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)i;
                     }
                 }
@@ -512,7 +546,7 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg)
         if (best_lr[gg] >= 0.0f) {
-            const unsigned long long key = make_key(best_lr[gg], best_at[gg]);
+            const unsigned long long key = make_key(0.5f * best_lr[gg], best_at[gg]);
             if (key > sm.best[g0 + gg][t]) sm.best[g0 + gg][t] = key;
         }
     return true;
@@ -570,7 +604,10 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
 #pragma unroll
                 for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
         }
+        bool ok = true;
         auto issue = [&](int sidx) {
+            if (iss.n >= FT_NSTAGE && !mbar_wait(&sm.empty[iss.stage], iss.parity ^ 1u))
+                return false;
             const int e0 = sidx * H;
             const int a = tmin[e0] & ~1;
             int end = 0;
@@ -582,12 +619,30 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
             mbar_expect_tx(&sm.bar[iss.stage], bytes);
             bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
             iss.next();
+            return true;
         };
-        if (t == 0)
-            for (int sidx = 0; sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx) issue(sidx);
-        for (int sidx = 0; live_epoch(sidx * H); ++sidx) {
-            if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H)) issue(sidx + FT_NSTAGE - 1);
-            const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
+        if (t < 32) {
+            bool iok = true;
+            if (t == 0)
+                for (int sidx = 0; iok && sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx)
+                    iok = issue(sidx);
+            ok = __shfl_sync(0xFFFFFFFFu, iok, 0);
+        }
+        for (int sidx = 0; ok && live_epoch(sidx * H); ++sidx) {
+            if (t < 32) {
+                bool iok = true;
+                if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H))
+                    iok = issue(sidx + FT_NSTAGE - 1);
+                if (!__shfl_sync(0xFFFFFFFFu, iok, 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(&sm.bar[con.stage], con.parity))) {
+                ok = false;
+                break;
+            }
+            const int stage = con.stage;
             const float2 *S = strips + con.stage * FT_STRIP - (tmin[sidx * H] & ~1);
             con.next();
 #pragma unroll
@@ -608,18 +663,21 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
                         add2(acc[gg][r], src[dg]);
                 }
             }
-            if (__syncthreads_or(!ok)) {
-                if (t == 0) {
-                    atomicExch(status, CETRA_ETIMEOUT);
-                    while (con.n < iss.n) {
-                        mbar_wait(&sm.bar[con.stage], con.parity);
-                        con.next();
-                    }
-                }
-                return false;
-            }
+            __syncwarp();
+            if ((t & 31) == 0) mbar_arrive(&sm.empty[stage]);
         }
-        // every copy is consumed: the strip ring is free to hold one period's partial sums
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(status, CETRA_ETIMEOUT);
+                while (con.n < iss.n) {
+                    mbar_wait(&sm.bar[con.stage], con.parity);
+                    con.next();
+                }
+            }
+            return false;
+        }
+        // every copy is consumed and every warp is past the barrier: the strip ring is free
+        // to hold one period's partial sums
         float2 *part = strips;
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg) {
@@ -818,7 +876,10 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
 
 __device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
     if (threadIdx.x == 0) {
-        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
+        for (int st = 0; st < FT_NSTAGE; ++st) {
+            mbar_init(&sm.bar[st], 1);
+            mbar_init(&sm.empty[st], FT_THREADS / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
