@@ -77,6 +77,29 @@ def dist_env():
     return rank, world, local
 
 
+def shard_range(n, rank, world):
+    """Contiguous share [a, b) of n independent curves for one rank (sizes differ by <= 1)."""
+    base, extra = divmod(n, world)
+    a = rank * base + min(rank, extra)
+    return a, a + base + (1 if rank < extra else 0)
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest of every rank's x (all_reduce MAX; x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(units_per_rank, world, t_max):
+    """Whole-job throughput: every rank's units / the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -508,12 +531,8 @@ def main():
     kern = {k: ctx.profile_read(k) for k in ("resample", "linear", "fold", "finalize")}
     ctx.profile(False)
     total_s = sum(step_ms) / 1e3
-    t_max = total_s
-    if world > 1:
-        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * args.steps / t_max
+    t_max = max_over_ranks(total_s, world, dev)
+    value = job_value(args.steps, world, t_max)
 
     # ------------------------------------------------------------------ e2e (host buffers)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -533,11 +552,7 @@ def main():
         if s > 0:  # the first call is a warm-up
             e2e_times.append(time.perf_counter() - t0)
     e2e_t = sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
-    e2e_value = world / e2e_t if world == 1 and e2e_times else None
-    if world > 1 and e2e_times:
-        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world / float(tt.item())
+    e2e_value = job_value(1, world, max_over_ranks(e2e_t, world, dev)) if e2e_times else None
     h2d = w.time.nbytes + w.flux.nbytes + w.flux_err.nbytes + w.periods.nbytes
     d2h = 5 * 8 * w.periods.size
 
