@@ -140,3 +140,42 @@ def test_batch_recovery_equals_plain_form():
             rec_p += hit(P[kp])
     assert rec_b == rec_p
     print(f"recovered {rec_b} of {n_inj} injected planets (batched) and {rec_p} (plain)")
+
+
+def test_batch_full_size_sampled():
+    """The 8,192-curve batch of the benchmark (1-13 sectors, autotuned launch shapes): the fold
+    of sampled 8-period groups of curves spread over the whole batch equals the oracle's best
+    over exactly those periods; curves without a sampled group are null."""
+    from paper_2503_20875_gb300 import Context, Batch
+    from paper_2503_20875_gb300.api import batch_period_grid
+    ws = synth.make_batch_workload(n_curves=8192, seed=1)
+    ctx = Context(0)
+    b = Batch(ctx, [(w.time, w.flux, w.flux_err) for w in ws], ws[0].durations, ws[0].template,
+              0.5, None, None, autotune=True, cadence=CAD, t0_step=STEP)
+    rng = np.random.default_rng(11)
+    pick = sorted(set(rng.choice(8192, 10, replace=False).tolist()) | {0, 8191})
+    items, chosen = [], {}
+    for c in pick:
+        g = b.curve(c)
+        groups = rng.choice(-(-g[3] // 8), 2, replace=False)
+        chosen[c] = (g, np.sort(groups))
+        items.extend(g[5] + np.sort(groups))
+    got = b.run_items(np.array(sorted(items)), linear=True)
+    for c in range(8192):
+        if c not in chosen:
+            assert got["k"][c] == -1
+    for c, (g, groups) in chosen.items():
+        w = ws[c]
+        P = batch_period_grid(g[1], g[2], g[3])
+        ks = np.concatenate([np.arange(8 * x, min(g[3], 8 * x + 8)) for x in groups])
+        r = oracle.search(w.time, w.flux, w.flux_err, w.durations, w.template, P[ks],
+                          cadence=CAD, t0_step=STEP)
+        per = r["periodic"]["dlogl"]
+        kb = int(np.nanargmax(per))
+        assert got["dlogl"][c] == pytest.approx(per[kb], rel=1e-5), c
+        if got["k"][c] != ks[kb] or got["i"][c] != r["periodic"]["i"][kb]:
+            m = list(ks).index(got["k"][c])
+            lr_at, _, _ = oracle.periodic_at(r["geom"], r["depth"], r["depth_var"], r["dlogl"],
+                                             P[[got["k"][c]]], [got["i"][c]], [got["j"][c]])
+            assert per[kb] - lr_at[0] <= 1e-5 * per[kb], c
+        assert got["period"][c] == P[got["k"][c]]
