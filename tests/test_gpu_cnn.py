@@ -57,7 +57,7 @@ def _layer_slices(cin):
     return out
 
 
-@pytest.mark.parametrize("cin,T,B", [(16, 512, 3), (1, 256, 2), (32, 768, 1)])
+@pytest.mark.parametrize("cin,T,B", [(16, 512, 3), (1, 256, 2), (32, 768, 1), (16, 4096, 2)])
 def test_forward_matches_oracle(cin, T, B):
     """Probabilities within 2e-5: FP32 sums of at most 288 BF16 x FP32 products per layer
     (relative error ~ 288 u_32 of the sum of magnitudes, ~2e-5 of a logit of order 1, and
@@ -72,7 +72,7 @@ def test_forward_matches_oracle(cin, T, B):
     np.testing.assert_allclose(d_p.cpu().numpy(), ref, rtol=0, atol=2e-5)
 
 
-@pytest.mark.parametrize("cin,T,B", [(16, 512, 3), (4, 256, 2)])
+@pytest.mark.parametrize("cin,T,B", [(16, 512, 3), (4, 256, 2), (16, 4096, 2)])
 def test_gradients_match_oracle(cin, T, B):
     """Loss to 1e-5 (relative) and every layer's gradient to 2e-3 of that layer's largest
     component (FP32 forward and backward sums; a ReLU whose input is within rounding of 0
