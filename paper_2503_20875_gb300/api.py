@@ -26,6 +26,30 @@ def _ptr(a):
     return ctypes.c_void_p(a.data_ptr())  # torch tensor
 
 
+def _dptr(t, dtype=None, numel=0, name="tensor", optional=False):
+    """Pointer of a device tensor after checking it: a contiguous CUDA torch tensor of the
+    given dtype (a torch dtype name) with at least `numel` elements. A host array or a short
+    buffer would reach a kernel as a bad address, so it is refused here."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    if not hasattr(t, "is_cuda") or not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and str(t.dtype) != "torch." + dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected torch.{dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {numel} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _wsb(ws):
+    """(pointer, bytes) of a device workspace tensor."""
+    return _dptr(ws, name="workspace"), ws.numel() * ws.element_size()
+
+
 def make_params(cadence=0.0, t0_step=0.0, template_samples=1024, flux_is_offset=False,
                 precision="fp32") -> N.cetra_params:
     p = N.cetra_params()
@@ -133,35 +157,45 @@ class Plan:
 # ----------------------------------------------------------------------------- device path
 
 def cetra_resample_device(ctx: Context, plan: Plan, d_time, d_flux, d_flux_err, workspace):
-    check(N.lib.cetra_resample_device(ctx.handle, plan.handle, _ptr(d_time), _ptr(d_flux),
-                                      _ptr(d_flux_err), int(d_time.numel()), _ptr(workspace),
-                                      workspace.numel() * workspace.element_size()),
+    n = int(d_time.numel())
+    ws, nb = _wsb(workspace)
+    check(N.lib.cetra_resample_device(ctx.handle, plan.handle, _dptr(d_time, "float64", n, "time"),
+                                      _dptr(d_flux, "float32", n, "flux"),
+                                      _dptr(d_flux_err, "float32", n, "flux_err"), n, ws, nb),
           ctx.handle, "resample_device")
 
 
 def cetra_linear_device(ctx: Context, plan: Plan, workspace, d_depth=None, d_depth_var=None,
                         d_dlogl=None):
-    check(N.lib.cetra_linear_device(ctx.handle, plan.handle, _ptr(workspace),
-                                    workspace.numel() * workspace.element_size(), _ptr(d_depth),
-                                    _ptr(d_depth_var), _ptr(d_dlogl)), ctx.handle, "linear_device")
+    cells = plan.info["n_dur"] * plan.info["n_t0"]
+    ws, nb = _wsb(workspace)
+    check(N.lib.cetra_linear_device(ctx.handle, plan.handle, ws, nb,
+                                    _dptr(d_depth, "float32", cells, "depth", True),
+                                    _dptr(d_depth_var, "float32", cells, "depth_var", True),
+                                    _dptr(d_dlogl, "float32", cells, "dlogl", True)),
+          ctx.handle, "linear_device")
 
 
 def cetra_periodic_device(ctx: Context, plan: Plan, workspace, d_periods, d_mask=None,
                           out: dict | None = None):
     out = out or {}
-    check(N.lib.cetra_periodic_device(ctx.handle, plan.handle, _ptr(workspace),
-                                      workspace.numel() * workspace.element_size(),
-                                      _ptr(d_periods), int(d_periods.numel()), _ptr(d_mask),
-                                      _ptr(out.get("dlogl")), _ptr(out.get("t0")),
-                                      _ptr(out.get("duration")), _ptr(out.get("depth")),
-                                      _ptr(out.get("depth_var")), _ptr(out.get("i")),
-                                      _ptr(out.get("j"))),
+    K = int(d_periods.numel())
+    ws, nb = _wsb(workspace)
+    o = {k: _dptr(out.get(k), dt, K, k, True) for k, dt in
+         (("dlogl", "float64"), ("t0", "float64"), ("duration", "float64"),
+          ("depth", "float64"), ("depth_var", "float64"), ("i", "int64"), ("j", "int32"))}
+    check(N.lib.cetra_periodic_device(ctx.handle, plan.handle, ws, nb,
+                                      _dptr(d_periods, "float64", K, "periods"), K,
+                                      _dptr(d_mask, "uint8", K * plan.info["n_dur"], "mask", True),
+                                      o["dlogl"], o["t0"], o["duration"], o["depth"],
+                                      o["depth_var"], o["i"], o["j"]),
           ctx.handle, "periodic_device")
 
 
 def cetra_logl0_device(ctx: Context, plan: Plan, workspace, d_out):
-    check(N.lib.cetra_logl0_device(ctx.handle, plan.handle, _ptr(workspace),
-                                   workspace.numel() * workspace.element_size(), _ptr(d_out)),
+    ws, nb = _wsb(workspace)
+    check(N.lib.cetra_logl0_device(ctx.handle, plan.handle, ws, nb,
+                                   _dptr(d_out, "float64", 1, "logl0")),
           ctx.handle, "logl0_device")
 
 
@@ -207,18 +241,23 @@ def cetra_mask_transits_device(ctx: Context, plan: Plan, d_workspace, period, t0
                                d_n_masked=None):
     """Null the resampled cells within half_width days of t0 + n period (then rerun
     cetra_linear_device)."""
-    check(N.lib.cetra_mask_transits_device(ctx.handle, plan.handle, _ptr(d_workspace),
-                                           d_workspace.numel() * d_workspace.element_size(),
-                                           float(period), float(t0), float(half_width),
-                                           _ptr(d_n_masked)), ctx.handle, "mask_transits_device")
+    ws, nb = _wsb(d_workspace)
+    check(N.lib.cetra_mask_transits_device(ctx.handle, plan.handle, ws, nb, float(period),
+                                           float(t0), float(half_width),
+                                           _dptr(d_n_masked, "int64", 1, "n_masked", True)),
+          ctx.handle, "mask_transits_device")
 
 
 def cetra_monotransits_device(ctx: Context, plan: Plan, d_workspace, max_events, d_events, d_n):
     """Single-transit events into d_events (a device byte tensor of max_events records)
     and d_n (device int32)."""
-    check(N.lib.cetra_monotransits_device(ctx.handle, plan.handle, _ptr(d_workspace),
-                                          d_workspace.numel() * d_workspace.element_size(),
-                                          int(max_events), _ptr(d_events), _ptr(d_n)),
+    ws, nb = _wsb(d_workspace)
+    rec = ctypes.sizeof(N.cetra_event)
+    if d_events is None or d_events.numel() * d_events.element_size() < int(max_events) * rec:
+        raise ValueError(f"events: needs {int(max_events) * rec} bytes of device memory")
+    check(N.lib.cetra_monotransits_device(ctx.handle, plan.handle, ws, nb, int(max_events),
+                                          _dptr(d_events, None, 0, "events"),
+                                          _dptr(d_n, "int32", 1, "n_events")),
           ctx.handle, "monotransits_device")
 
 
@@ -413,7 +452,8 @@ class Batch:
                               device=torch.device("cuda", self.ctx.device))
         elif tuple(out.shape) != (self.n, J, n_bins) or not out.is_contiguous():
             raise ValueError("out must be a contiguous [n_curves][n_dur][n_bins] tensor")
-        check(N.lib.cetra_batch_features(self.ctx.handle, self.handle, int(n_bins), _ptr(out)),
+        check(N.lib.cetra_batch_features(self.ctx.handle, self.handle, int(n_bins),
+                                         _dptr(out, "float32", self.n * J * n_bins, "out")),
               self.ctx.handle, "batch_features")
         return out
 
@@ -443,7 +483,9 @@ class Batch:
         best = (N.cetra_best * self.n)()
         n_it, n_per = ctypes.c_int64(), ctypes.c_int64()
         buf = np.empty(max(1, self.info["n_fold_items"]), np.int64) if items else None
-        check(N.lib.cetra_batch_run_proposed(self.ctx.handle, self.handle, _ptr(d_scores),
+        n_int = int(d_scores.shape[1]) if d_scores.dim() == 2 else 0
+        check(N.lib.cetra_batch_run_proposed(self.ctx.handle, self.handle,
+                                             _dptr(d_scores, "float32", self.n * n_int, "scores"),
                                              int(d_scores.shape[1]), float(p_lo), float(p_hi),
                                              float(top_frac), int(bool(linear)), best,
                                              ctypes.byref(n_it), ctypes.byref(n_per), _ptr(buf)),
@@ -507,16 +549,25 @@ class CNN:
         assert p.size == self.n_params
         check(N.lib.cetra_cnn_set_params(self.ctx.handle, self.handle, _ptr(p)), self.ctx.handle)
 
+    def _features(self, d_features):
+        if tuple(d_features.shape[1:]) != (self.in_channels, self.n_bins):
+            raise ValueError(f"features: shape {tuple(d_features.shape)}, expected "
+                             f"[B][{self.in_channels}][{self.n_bins}]")
+        B = int(d_features.shape[0])
+        return B, _dptr(d_features, "float32", B * self.in_channels * self.n_bins, "features")
+
     def forward(self, d_features, d_prob):
-        check(N.lib.cetra_cnn_forward(self.ctx.handle, self.handle, _ptr(d_features),
-                                      int(d_features.shape[0]), _ptr(d_prob)), self.ctx.handle,
-              "cnn_forward")
+        B, f = self._features(d_features)
+        check(N.lib.cetra_cnn_forward(self.ctx.handle, self.handle, f, B,
+                                      _dptr(d_prob, "float32", B * self.n_bins, "prob")),
+              self.ctx.handle, "cnn_forward")
 
     def backward(self, d_features, d_labels, pos_weight=20.0, grads=False):
         loss = ctypes.c_double(0.0)
         g = np.empty(self.n_params, np.float32) if grads else None
-        check(N.lib.cetra_cnn_backward(self.ctx.handle, self.handle, _ptr(d_features),
-                                       _ptr(d_labels), int(d_features.shape[0]),
+        B, f = self._features(d_features)
+        check(N.lib.cetra_cnn_backward(self.ctx.handle, self.handle, f,
+                                       _dptr(d_labels, "float32", B * self.n_bins, "labels"), B,
                                        float(pos_weight), ctypes.byref(loss), _ptr(g)),
               self.ctx.handle, "cnn_backward")
         return (loss.value, g) if grads else loss.value
@@ -539,14 +590,18 @@ class CNN:
 
 def cetra_cnn_map(ctx: Context, d_prob, d_features, d_map):
     """d_map = d_prob * sqrt(2 * max over durations of d_features) (device tensors)."""
-    B, J, T = d_features.shape
-    check(N.lib.cetra_cnn_map(ctx.handle, _ptr(d_prob), _ptr(d_features), int(B), int(J), int(T),
-                              _ptr(d_map)), ctx.handle, "cnn_map")
+    B, J, T = (int(x) for x in d_features.shape)
+    check(N.lib.cetra_cnn_map(ctx.handle, _dptr(d_prob, "float32", B * T, "prob"),
+                              _dptr(d_features, "float32", B * J * T, "features"), B, J, T,
+                              _dptr(d_map, "float32", B * T, "map")), ctx.handle, "cnn_map")
 
 
 def cetra_cnn_comb(ctx: Context, d_map, d_bin_days, p_lo, p_hi, n_intervals, d_scores,
                    d_n_valid=None):
-    B, T = d_map.shape
-    check(N.lib.cetra_cnn_comb(ctx.handle, _ptr(d_map), int(B), int(T), _ptr(d_bin_days),
-                               _ptr(d_n_valid), float(p_lo), float(p_hi), int(n_intervals),
-                               _ptr(d_scores)), ctx.handle, "cnn_comb")
+    B, T = (int(x) for x in d_map.shape)
+    check(N.lib.cetra_cnn_comb(ctx.handle, _dptr(d_map, "float32", B * T, "map"), B, T,
+                               _dptr(d_bin_days, "float64", B, "bin_days"),
+                               _dptr(d_n_valid, "int32", B, "n_valid", True), float(p_lo),
+                               float(p_hi), int(n_intervals),
+                               _dptr(d_scores, "float32", B * int(n_intervals), "scores")),
+          ctx.handle, "cnn_comb")

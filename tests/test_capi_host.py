@@ -101,3 +101,17 @@ def test_context_creation_without_gpu_fails_cleanly():
     h = ctypes.c_void_p()
     assert N.lib.cetra_create(ctypes.byref(h), 0, None) == N.CETRA_ECUDA
     assert not h.value
+
+
+def test_binding_refuses_host_and_short_buffers():
+    """Device arguments are checked in the binding before any call: host arrays, CPU tensors,
+    wrong dtypes, non-contiguous views and short buffers never reach a kernel."""
+    torch = pytest.importorskip("torch")
+    from paper_2503_20875_gb300 import api
+    with pytest.raises(ValueError):
+        api._dptr(np.zeros(4, np.float32), "float32", 4, "x")
+    with pytest.raises(ValueError):
+        api._dptr(torch.zeros(4), "float32", 4, "x")
+    with pytest.raises(ValueError):
+        api._dptr(None, "float32", 4, "x")
+    assert api._dptr(None, "float32", 4, "x", optional=True) is None
