@@ -552,21 +552,29 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
     return true;
 }
 
-// A sub-group whose periods all have few phases (nph <= Tp <= T/2, Tp a power of two):
-// the lanes L = t + FT_THREADS r of the block form H = T / Tp epoch slices of Tp phases;
-// slice h folds epochs e = s H + h of super-epoch s, and one bulk copy per super-epoch
-// covers its H epochs. The H partial sums of every phase are then added in slice order
-// through shared memory. (Strip bound: tmin grows by at most Tp + 1 per epoch, so a
-// super-epoch needs at most T + spread + 3 cells; the table check keeps spread <=
-// FT_STRIP - FT_T - 8 for this path.)
+// A sub-group whose periods all have few phases (nph <= Tp <= T/2, Tp = max(32, nph)):
+// the lanes L = t + FT_THREADS r of the block form H = floor(T / Tp) epoch slices of Tp
+// phases (lane L: slice L / Tp, phase L % Tp; lanes past H Tp idle); slice h folds epochs
+// e = s H + h of super-epoch s, and one bulk copy per super-epoch covers its H epochs. The
+// H partial sums of every phase are then added in slice order through shared memory.
+// (Strip bound: tmin grows by at most Tp per epoch (o_{e+1} - o_e <= ceil(Ps) <= Tp for the
+// period that attains tmin[e]), so a super-epoch needs at most H Tp + spread + 2 <=
+// T + spread + 2 cells; the table check keeps spread <= FT_STRIP - FT_T - 8 for this path.)
 template <int GS, int R, bool KAHAN>
 __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_t *tab, int Es,
                                      int g0, int mask_k0, const float2 *__restrict__ ab, int I,
                                      int64_t ld, int J, const double *__restrict__ durations,
                                      const uint8_t *__restrict__ mask, ring &iss, ring &con,
-                                     int *__restrict__ status, int tp_log2) {
+                                     int *__restrict__ status, int Tp) {
     constexpr int T = FT_THREADS * R;
-    const int Tp = 1 << tp_log2, H = T >> tp_log2;
+    const int H = T / Tp;
+    int slice[R], phase[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int L = threadIdx.x + r * FT_THREADS;
+        slice[r] = L / Tp;
+        phase[r] = L - slice[r] * Tp;
+    }
     const int t = threadIdx.x;
     const int32_t *d = tab;
     const int32_t *tmin = tab + Es * GS;
@@ -647,10 +655,10 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
             con.next();
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int L = t + r * FT_THREADS;
-                const int e = sidx * H + (L >> tp_log2);
+                if (slice[r] >= H) continue;  // lane past the last whole slice
+                const int e = sidx * H + slice[r];
                 if (!live_epoch(e)) continue;
-                const float2 *src = S + (L & (Tp - 1)) + tmin[e];
+                const float2 *src = S + phase[r] + tmin[e];
                 const int32_t *de = d + e * GS;
                 const bool fast = all_used && full[e];
 #pragma unroll
@@ -831,10 +839,9 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
         // periods with few phases: fold several epochs at once (epoch slices)
         int nph_sub = 0;
         for (int g = g0; g < g0 + Gs; ++g) nph_sub = max(nph_sub, sm.nph[g]);
-        int tp_log2 = 5;
-        while ((1 << tp_log2) < nph_sub) ++tp_log2;
+        const int tp = max(32, nph_sub);  // phases per epoch slice
         const bool sliced = table_ok && !sm.tight && nph_sub > 0 &&
-                            (2 << tp_log2) <= FT_THREADS * R;
+                            2 * tp <= FT_THREADS * R;
         bool ok = true;
         if (!table_ok) {
             fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, durations, mask);
@@ -842,19 +849,19 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
             if (Gs == 8)
                 ok = fold_subgroup_sliced<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
                                                        ld, J, durations, mask, iss, con, status,
-                                                       tp_log2);
+                                                       tp);
             else if (Gs == 4)
                 ok = fold_subgroup_sliced<4, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
                                                        ld, J, durations, mask, iss, con, status,
-                                                       tp_log2);
+                                                       tp);
             else if (Gs == 2)
                 ok = fold_subgroup_sliced<2, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
                                                        ld, J, durations, mask, iss, con, status,
-                                                       tp_log2);
+                                                       tp);
             else
                 ok = fold_subgroup_sliced<1, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
                                                        ld, J, durations, mask, iss, con, status,
-                                                       tp_log2);
+                                                       tp);
         } else if (Gs == 8) {
             ok = fold_subgroup<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
                                             durations, mask, iss, con, status);
