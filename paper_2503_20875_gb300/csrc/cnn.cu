@@ -253,14 +253,19 @@ __global__ void cnn_map_kernel(const float *__restrict__ prob, const float *__re
 // skipped. Epochs run in 32.32 fixed point: F = floor(Pb 2^32 + 1/2), and for each phase
 // ph < ceil(Pb) the epochs are t_e = (ph 2^32 + e F + 2^31) >> 32 < V; the score is
 // sum_e p[t_e] / sqrt(E). The interval's score is the best of those, and 0 if none is positive.
-// One block per (interval, curve); the curve's map is staged in shared memory when it fits,
-// and the block's threads share the (trial, phase) pairs, consecutive lanes taking
-// consecutive phases of one trial.
+// One block per (interval, curve); the curve's map is staged in shared memory when it fits.
+// The trials' FP64 arithmetic (Pb, F, phase count) is done once per trial into shared memory,
+// COMB_CHUNK trials at a time; the block's threads then share the (trial, phase) pairs of the
+// chunk (consecutive lanes take consecutive phases of one trial) with 32-bit index arithmetic
+// and a 64-bit fixed-point epoch loop.
+constexpr int COMB_CHUNK = 256;
 template <bool SMEM>
 __global__ void cnn_comb_kernel(const float *__restrict__ p, const double *__restrict__ bw,
                                 const int *__restrict__ n_valid, int T, double p_lo,
                                 double p_hi, int n_int, float *__restrict__ scores) {
     extern __shared__ float cmap[];
+    __shared__ unsigned long long trial_F[COMB_CHUNK];
+    __shared__ uint32_t trial_nph[COMB_CHUNK];
     const int b = blockIdx.y, q = blockIdx.x;
     const int V = n_valid ? min(max(n_valid[b], 0), T) : T;
     const float *pb = p + (int64_t)b * T;
@@ -274,22 +279,35 @@ __global__ void cnn_comb_kernel(const float *__restrict__ p, const double *__res
     const double w = bw[b];
     float best = 0.0f;
     const double blo = w > 0.0 ? lo / w : 0.0, bhi = w > 0.0 ? hi / w : 0.0;  // in bins
-    if (w > 0.0 && V > 0 && bhi >= 1.0 && blo <= 0.5 * (double)V) {
+    if (w > 0.0 && V > 0 && bhi >= 1.0 && blo <= 0.5 * (double)V) {  // uniform over the block
         const int64_t nP = max((int64_t)1, (int64_t)ceil((bhi - blo) * (double)V / blo));
-        const int64_t nph = (int64_t)ceil(fmin(bhi, 0.5 * (double)V));  // phases of the longest trial
+        // phases of the longest trial (<= V / 2 < 2^30)
+        const uint32_t nph = (uint32_t)ceil(fmin(bhi, 0.5 * (double)V));
         const uint64_t end = (uint64_t)V << 32;
-        for (int64_t x = threadIdx.x; x < nP * nph; x += blockDim.x) {
-            const int64_t m = x / nph, ph = x % nph;
-            const double Pb = blo + (bhi - blo) * ((double)m + 0.5) / (double)nP;
-            if (Pb < 1.0 || Pb > 0.5 * (double)V || (double)ph >= ceil(Pb)) continue;
-            const uint64_t F = (uint64_t)floor(Pb * 4294967296.0 + 0.5);
-            float s = 0.0f;
-            int E = 0;
-            for (uint64_t acc = ((uint64_t)ph << 32) + (1ull << 31); acc < end; acc += F) {
-                s += src[acc >> 32];
-                ++E;
+        const int64_t per_chunk = min((int64_t)COMB_CHUNK, (int64_t)(0xFFFFFFFFu / nph));
+        for (int64_t m0 = 0; m0 < nP; m0 += per_chunk) {
+            const int cnt = (int)min(per_chunk, nP - m0);
+            __syncthreads();  // the previous chunk's trials are no longer read
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const double Pb = blo + (bhi - blo) * ((double)(m0 + i) + 0.5) / (double)nP;
+                const bool ok = Pb >= 1.0 && Pb <= 0.5 * (double)V;
+                trial_F[i] = ok ? (unsigned long long)floor(Pb * 4294967296.0 + 0.5) : 0ull;
+                trial_nph[i] = ok ? (uint32_t)ceil(Pb) : 0u;
             }
-            if (E > 0) best = fmaxf(best, s / sqrtf((float)E));
+            __syncthreads();
+            const uint32_t pairs = (uint32_t)cnt * nph;
+            for (uint32_t x = threadIdx.x; x < pairs; x += blockDim.x) {
+                const uint32_t m = x / nph, ph = x - m * nph;
+                if (ph >= trial_nph[m]) continue;
+                const unsigned long long F = trial_F[m];
+                float s = 0.0f;
+                int E = 0;
+                for (uint64_t acc = ((uint64_t)ph << 32) + (1ull << 31); acc < end; acc += F) {
+                    s += src[acc >> 32];
+                    ++E;
+                }
+                best = fmaxf(best, s / sqrtf((float)E));  // E >= 1: ph < ceil(Pb) <= V/2
+            }
         }
     }
     __shared__ float red[32];
