@@ -56,6 +56,10 @@ struct cetra_plan {
     // device copies (owned)
     double *d_durations = nullptr;
     int32_t *d_win_a = nullptr, *d_win_len = nullptr, *d_win_padlen = nullptr;
+    // linear-stage rows (duration, phase class) by decreasing window length: the kernel takes
+    // its longest blocks first, so the last wave holds the shortest ones
+    std::vector<int32_t> lin_order;
+    int32_t *d_lin_order = nullptr;
     int64_t *d_win_off = nullptr;
     float2 *d_tables = nullptr;
 };

@@ -121,14 +121,17 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
 // window over the span and accumulates RB outputs (A, B) with packed FP32x2 FMAs.
 // For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
 // KAHAN: every term is added with Kahan compensation (CETRA_FP32_KAHAN).
-template <int RB, bool KAHAN>
+template <int RB, bool KAHAN, int PFIX>
 __device__ __forceinline__ void linear_block(int tile, int jr, const float *__restrict__ wy,
               const float *__restrict__ w, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
-              const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
-              int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
+              const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off,
+              int p_arg, int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
               float *__restrict__ depth,
               float *__restrict__ var, float *__restrict__ dlogl) {
+    // PFIX = 1: the t0 step equals the cadence (p = 1, the common case), known at compile time
+    // so that the inner loop's shared-memory offsets are immediates
+    const int p = PFIX ? PFIX : p_arg;
     extern __shared__ float2 smem[];
     const int nthr = blockDim.x;
     const int t = threadIdx.x;
@@ -222,14 +225,23 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float *__re
 }
 
 template <int RB, bool KAHAN>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
               const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
-              int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
-              float *__restrict__ depth, float *__restrict__ var, float *__restrict__ dlogl) {
-    linear_block<RB, KAHAN>(blockIdx.x, blockIdx.y, wy, w, n_grid, tables, win_a, win_padlen,
-                            win_off, p, q, I, ld, kc_max, ab, depth, var, dlogl);
+              int q, int64_t I, int64_t ld, int kc_max, const int32_t *__restrict__ order,
+              float2 *__restrict__ ab, float *__restrict__ depth, float *__restrict__ var,
+              float *__restrict__ dlogl) {
+    // rows by decreasing window length: blocks are dispatched in y-major order, so the
+    // longest blocks start first and the last wave holds the shortest ones
+    if (p == 1)
+        linear_block<RB, KAHAN, 1>(blockIdx.x, order[blockIdx.y], wy, w, n_grid, tables, win_a,
+                                   win_padlen, win_off, p, q, I, ld, kc_max, ab, depth, var,
+                                   dlogl);
+    else
+        linear_block<RB, KAHAN, 0>(blockIdx.x, order[blockIdx.y], wy, w, n_grid, tables, win_a,
+                                   win_padlen, win_off, p, q, I, ld, kc_max, ab, depth, var,
+                                   dlogl);
 }
 
 // Per-period key: larger LR wins; on equal LR the smaller flat index j*I + i wins
@@ -1046,19 +1058,26 @@ __global__ void batch_resample_kernel(const double *__restrict__ time,
 
 // Sec. 2.2 for every curve: x-blocks enumerate the t0 tiles of all curves.
 template <int RB, bool KAHAN>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 batch_linear_kernel(const int64_t *__restrict__ tile_off, int n_curves,
                     const batch_curve *__restrict__ curves, const float *__restrict__ wy,
                     const float *__restrict__ w, const float2 *__restrict__ tables,
                     const int32_t *__restrict__ win_a, const int32_t *__restrict__ win_padlen,
                     const int64_t *__restrict__ win_off, int p, int q, int kc_max,
-                    float2 *__restrict__ ab) {
+                    const int32_t *__restrict__ order, float2 *__restrict__ ab) {
     const int cidx = csr_find(tile_off, n_curves, blockIdx.x);
     const batch_curve cv = curves[cidx];
     if (cv.I <= 0) return;
-    linear_block<RB, KAHAN>((int)(blockIdx.x - tile_off[cidx]), blockIdx.y, wy + cv.grid_off,
-                            w + cv.grid_off, cv.n_grid, tables, win_a, win_padlen, win_off, p, q,
-                            cv.I, cv.ld, kc_max, ab + cv.ab_off, nullptr, nullptr, nullptr);
+    if (p == 1)
+        linear_block<RB, KAHAN, 1>((int)(blockIdx.x - tile_off[cidx]), order[blockIdx.y],
+                                   wy + cv.grid_off, w + cv.grid_off, cv.n_grid, tables, win_a,
+                                   win_padlen, win_off, p, q, cv.I, cv.ld, kc_max,
+                                   ab + cv.ab_off, nullptr, nullptr, nullptr);
+    else
+        linear_block<RB, KAHAN, 0>((int)(blockIdx.x - tile_off[cidx]), order[blockIdx.y],
+                                   wy + cv.grid_off, w + cv.grid_off, cv.n_grid, tables, win_a,
+                                   win_padlen, win_off, p, q, cv.I, cv.ld, kc_max,
+                                   ab + cv.ab_off, nullptr, nullptr, nullptr);
 }
 
 // Sec. 2.3 for every curve: persistent blocks drain a queue of (curve, group of FT_G
@@ -1357,7 +1376,8 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
                                                     : linear_kernel<LIN_RB, false>;
     kern<<<grid, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
         wy, w, plan->n_grid, plan->d_tables, plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
-        (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, ab, depth, var, dlogl);
+        (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, plan->d_lin_order, ab, depth, var,
+        dlogl);
     prof_mark(ctx, KID_LINEAR, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -1448,7 +1468,8 @@ cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int
                                                     : batch_linear_kernel<LIN_RB, false>;
     kern<<<grid, threads, smem, stream>>>(tile_off, n_curves, curves, wy, w, plan->d_tables,
                                           plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
-                                          (int)plan->p, (int)plan->q, plan->lin_kc, ab);
+                                          (int)plan->p, (int)plan->q, plan->lin_kc,
+                                          plan->d_lin_order, ab);
     return cudaGetLastError();
 }
 

@@ -233,6 +233,13 @@ int plan_upload(cetra_ctx *ctx, cetra_plan *plan) {
     if ((rc = upload(ctx, &plan->d_win_padlen, plan->win_padlen.data(), plan->win_padlen.size())))
         return rc;
     if ((rc = upload(ctx, &plan->d_win_off, plan->win_off.data(), plan->win_off.size()))) return rc;
+    plan->lin_order.resize(plan->win_padlen.size());
+    for (size_t x = 0; x < plan->lin_order.size(); ++x) plan->lin_order[x] = (int32_t)x;
+    std::stable_sort(plan->lin_order.begin(), plan->lin_order.end(), [&](int32_t a, int32_t b) {
+        return plan->win_padlen[(size_t)a] > plan->win_padlen[(size_t)b];
+    });
+    if ((rc = upload(ctx, &plan->d_lin_order, plan->lin_order.data(), plan->lin_order.size())))
+        return rc;
     if ((rc = upload(ctx, &plan->d_tables, plan->tables.data(), plan->tables.size()))) return rc;
     cudaError_t e = linear_configure(plan, ctx);
     if (e != cudaSuccess) return set_error(ctx, CETRA_ECUDA, cudaGetErrorString(e));
@@ -245,10 +252,12 @@ void plan_free_device(cetra_plan *plan) {
     cudaFree(plan->d_win_len);
     cudaFree(plan->d_win_padlen);
     cudaFree(plan->d_win_off);
+    cudaFree(plan->d_lin_order);
     cudaFree(plan->d_tables);
     plan->d_durations = nullptr;
     plan->d_win_a = plan->d_win_len = plan->d_win_padlen = nullptr;
     plan->d_win_off = nullptr;
+    plan->d_lin_order = nullptr;
     plan->d_tables = nullptr;
 }
 
