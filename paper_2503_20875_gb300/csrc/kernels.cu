@@ -121,6 +121,7 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
 // window over the span and accumulates RB outputs (A, B) with packed FP32x2 FMAs.
 // For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
 // KAHAN: every term is added with Kahan compensation (CETRA_FP32_KAHAN).
+constexpr int LIN_STAGE_U = 4;  // staging loads in flight per thread (linear kernel)
 template <int RB, bool KAHAN, int PFIX>
 __device__ __forceinline__ void linear_block(int tile, int jr, const float *__restrict__ wy,
               const float *__restrict__ w, int64_t n_grid,
@@ -157,14 +158,31 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float *__re
     for (int kc0 = 0; kc0 < padlen; kc0 += kc_max) {
         const int kcl = min(kc_max, padlen - kc0);
         __syncthreads();
-        for (int idx = t; idx < kcl; idx += nthr) st[idx] = tab[kc0 + idx];
+        // staging: LIN_STAGE_U cells per thread in flight before the shared stores
+        for (int idx0 = t; idx0 < kcl; idx0 += LIN_STAGE_U * nthr) {
+            float2 v[LIN_STAGE_U];
+#pragma unroll
+            for (int u = 0; u < LIN_STAGE_U; ++u) {
+                const int idx = idx0 + u * nthr;
+                v[u] = idx < kcl ? tab[kc0 + idx] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < LIN_STAGE_U; ++u)
+                if (idx0 + u * nthr < kcl) st[idx0 + u * nthr] = v[u];
+        }
         const int64_t base = a0 + kc0;
         const int dl = (int)(p * UT) + kcl;
-        for (int idx = t; idx < dl; idx += nthr) {
-            const int64_t n = base + idx;
-            float2 v = make_float2(0.f, 0.f);
-            if (n >= 0 && n < n_grid) v = make_float2(wy[n], w[n]);
-            sd[idx] = v;
+        for (int idx0 = t; idx0 < dl; idx0 += LIN_STAGE_U * nthr) {
+            float2 v[LIN_STAGE_U];
+#pragma unroll
+            for (int u = 0; u < LIN_STAGE_U; ++u) {
+                const int64_t n = base + idx0 + u * nthr;
+                v[u] = make_float2(0.f, 0.f);
+                if (idx0 + u * nthr < dl && n >= 0 && n < n_grid) v[u] = make_float2(wy[n], w[n]);
+            }
+#pragma unroll
+            for (int u = 0; u < LIN_STAGE_U; ++u)
+                if (idx0 + u * nthr < dl) sd[idx0 + u * nthr] = v[u];
         }
         __syncthreads();
         const int nk1 = kcl / p;  // a multiple of RB (tables are padded to p*RB)
