@@ -492,10 +492,11 @@ int cetra_cnn_set_params(cetra_ctx *ctx, cetra_cnn *n, const float *host) {
     cudaError_t e = cudaMemcpyAsync(n->d_params, host, (size_t)n->n_params * 4,
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (!e) e = round_weights(ctx, n);
+    // new parameters start a new optimisation: clear Adam's moments and step count
+    if (!e) e = cudaMemsetAsync(n->d_m, 0, (size_t)n->n_params * 4, ctx->stream);
+    if (!e) e = cudaMemsetAsync(n->d_v, 0, (size_t)n->n_params * 4, ctx->stream);
     if (!e) e = cudaStreamSynchronize(ctx->stream);
     n->adam_step = 0;
-    cudaMemsetAsync(n->d_m, 0, (size_t)n->n_params * 4, ctx->stream);
-    cudaMemsetAsync(n->d_v, 0, (size_t)n->n_params * 4, ctx->stream);
     return e ? cnn_fail(ctx, e, "cnn_set_params") : CETRA_OK;
 }
 
