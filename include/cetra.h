@@ -395,26 +395,35 @@ int cetra_search_batch(cetra_ctx *ctx, const cetra_params *params, int n_curves,
  * ------------------------------------------------------------------------------------- */
 typedef struct cetra_cnn cetra_cnn;
 
-/* in_channels 1..32 (the durations), n_bins a multiple of 256, He-normal initial weights
- * from `seed`. Device buffers sized for max_batch curves. */
+/* Create a network for in_channels 1..32 (the durations) and n_bins (a multiple of 256) per
+ * curve, He-normal initial weights from `seed` (zero biases); the network owns device buffers
+ * for max_batch curves (activations, gradients, Adam state). Blocks. Errors: CETRA_EINVAL
+ * (sizes), CETRA_ENOMEM, CETRA_ECUDA. Release with cetra_cnn_destroy (NULL allowed). */
 int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch, uint64_t seed,
                      cetra_cnn **cnn);
 void cetra_cnn_destroy(cetra_cnn *cnn);
+/* Number of FP32 parameters (the length of host_params / host_grads below). */
 int64_t cetra_cnn_param_count(const cetra_cnn *cnn);
+/* Copy the FP32 training copy of the parameters to host_params (caller-owned). Blocks. */
 int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *cnn, float *host_params);
-/* Replaces the parameters and resets the optimiser state. */
+/* Replace the parameters from host_params, re-round the BF16 weights and reset the optimiser
+ * state (moments and step count). Blocks. */
 int cetra_cnn_set_params(cetra_ctx *ctx, cetra_cnn *cnn, const float *host_params);
-/* d_features: device [B][in][n_bins]; d_prob: device [B][n_bins], sigmoid of the logits. */
+/* Probabilities for B <= max_batch curves: d_features device FP32 [B][in][n_bins] (read only),
+ * d_prob device FP32 [B][n_bins] (written), both caller-owned. Asynchronous on the context's
+ * stream. Errors: CETRA_EINVAL (NULL pointers, B outside 1..max_batch), CETRA_ECUDA. */
 int cetra_cnn_forward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features, int B,
                       float *d_prob);
 /* Forward + backward of the weighted binary cross-entropy with logits against d_labels
- * (device [B][n_bins], 0 or 1), mean over bins, positive weight pos_weight. Leaves the
+ * (device FP32 [B][n_bins], 0 or 1), mean over bins, positive weight pos_weight. Leaves the
  * gradient on the device for cetra_cnn_adam; *loss and host_grads (flat, like the
- * parameters) are filled when not NULL (that synchronises). */
+ * parameters) are filled when not NULL (that synchronises). Weight gradients are summed with
+ * atomics, so their last bits may differ from run to run. Errors as cetra_cnn_forward. */
 int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features,
                        const float *d_labels, int B, float pos_weight, double *loss,
                        float *host_grads);
-/* One Adam step with the last gradient (bias-corrected), then re-rounds the BF16 weights. */
+/* One bias-corrected Adam step with the last gradient on the FP32 parameters, then the BF16
+ * weights are re-rounded. Asynchronous. */
 int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *cnn, float lr, float beta1, float beta2,
                    float eps);
 /* Proposal map d_map[b][t] = d_prob[b][t] * sqrt(2 max_j max(d_features[b][j][t], 0)): the
