@@ -300,10 +300,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                  : "memory");
 }
-// Arrive on a barrier (release: the thread's earlier shared-memory reads are done).
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -364,8 +360,7 @@ constexpr int32_t FT_SENT = INT32_MAX;  // epoch past the end of the t0 grid
 
 // Shared state of the fold block.
 struct fold_smem {
-    uint64_t bar[FT_NSTAGE];    // stage filled (bulk copy landed)
-    uint64_t empty[FT_NSTAGE];  // stage drained (every warp done reading it)
+    uint64_t bar[FT_NSTAGE];  // stage filled (bulk copy landed)
     unsigned long long red[FT_THREADS / 32];
     unsigned long long best[FT_G][FT_THREADS];
     double P[FT_G], Ps[FT_G];
@@ -377,9 +372,10 @@ struct fold_smem {
 
 // Ring of bulk copies: `n` counts copies issued (thread 0) or consumed (all threads);
 // copy n lands in stage n % FT_NSTAGE, completing phase n / FT_NSTAGE of that stage's `bar`.
-// Every warp arrives on the stage's `empty` barrier once it has read the stage, and thread 0
-// waits for that phase before the stage takes copy n + FT_NSTAGE, so warps run up to
-// FT_NSTAGE - 1 epochs apart instead of meeting at a block barrier every epoch.
+// The block meets at a barrier after every epoch (which also votes on wait time-outs), so
+// thread 0 may refill the stage read two epochs earlier. (Per-stage drain barriers instead,
+// with warps drifting up to two epochs apart, measured 0.6-2 % faster on the largest
+// workloads but 11-13 % slower on small ones and on the compensated path.)
 struct ring {
     uint32_t n = 0, stage = 0, parity = 0;
     __device__ void next() {
@@ -463,11 +459,7 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
             }
             // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
             auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
-            bool ok = true;
-            // (thread 0) copy epoch e's strip once every warp has drained the stage
             auto issue = [&](int e) {
-                if (iss.n >= FT_NSTAGE && !mbar_wait(&sm.empty[iss.stage], iss.parity ^ 1u))
-                    return false;
                 const int a = (i0 + tmin[e]) & ~1;
                 const int len = ((i0 + tmin[e] + tlen[e] + T - a) + 1) & ~1;
                 const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
@@ -475,31 +467,12 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                 mbar_expect_tx(&sm.bar[iss.stage], bytes);
                 bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
                 iss.next();
-                return true;
             };
-            // every decision that ends the loop is uniform within a warp (the warp's lanes
-            // meet in __syncwarp below): warp 0 learns thread 0's issue outcome by shuffle,
-            // and a warp stops if any of its lanes' waits ran out
-            if (t < 32) {
-                bool iok = true;
-                if (t == 0)
-                    for (int e = 0; iok && e < FT_NSTAGE - 1 && live(e); ++e) iok = issue(e);
-                ok = __shfl_sync(0xFFFFFFFFu, iok, 0);
-            }
-            for (int e = 0; ok && live(e); ++e) {
-                if (t < 32) {
-                    bool iok = true;
-                    if (t == 0 && live(e + FT_NSTAGE - 1)) iok = issue(e + FT_NSTAGE - 1);
-                    if (!__shfl_sync(0xFFFFFFFFu, iok, 0)) {
-                        ok = false;
-                        break;
-                    }
-                }
-                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&sm.bar[con.stage], con.parity))) {
-                    ok = false;
-                    break;
-                }
-                const int stage = con.stage;
+            if (t == 0)
+                for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
+            for (int e = 0; live(e); ++e) {
+                if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
+                const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
                 const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
                 con.next();
                 const int32_t *de = d + e * GS;
@@ -538,19 +511,17 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                         }
                     }
                 }
-                __syncwarp();
-                if ((t & 31) == 0) mbar_arrive(&sm.empty[stage]);
-            }
-            if (__syncthreads_or(!ok)) {
-                // a wait ran out: record it, drain the copies in flight, stop
-                if (t == 0) {
-                    atomicExch(status, CETRA_ETIMEOUT);
-                    while (con.n < iss.n) {
-                        mbar_wait(&sm.bar[con.stage], con.parity);
-                        con.next();
+                if (__syncthreads_or(!ok)) {
+                    // a copy did not land in time: record it, drain the ring, stop
+                    if (t == 0) {
+                        atomicExch(status, CETRA_ETIMEOUT);
+                        while (con.n < iss.n) {
+                            mbar_wait(&sm.bar[con.stage], con.parity);
+                            con.next();
+                        }
                     }
+                    return false;
                 }
-                return false;
             }
             // 2 LR = SA^2 / SB per (period, phase) (a null sum gives NaN, never a maximum);
             // the running max keeps the first (smallest j, then smallest i) of equal values
@@ -642,10 +613,7 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
 #pragma unroll
                 for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
         }
-        bool ok = true;
         auto issue = [&](int sidx) {
-            if (iss.n >= FT_NSTAGE && !mbar_wait(&sm.empty[iss.stage], iss.parity ^ 1u))
-                return false;
             const int e0 = sidx * H;
             const int a = tmin[e0] & ~1;
             int end = 0;
@@ -657,30 +625,12 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
             mbar_expect_tx(&sm.bar[iss.stage], bytes);
             bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
             iss.next();
-            return true;
         };
-        if (t < 32) {
-            bool iok = true;
-            if (t == 0)
-                for (int sidx = 0; iok && sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx)
-                    iok = issue(sidx);
-            ok = __shfl_sync(0xFFFFFFFFu, iok, 0);
-        }
-        for (int sidx = 0; ok && live_epoch(sidx * H); ++sidx) {
-            if (t < 32) {
-                bool iok = true;
-                if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H))
-                    iok = issue(sidx + FT_NSTAGE - 1);
-                if (!__shfl_sync(0xFFFFFFFFu, iok, 0)) {
-                    ok = false;
-                    break;
-                }
-            }
-            if (!__all_sync(0xFFFFFFFFu, mbar_wait(&sm.bar[con.stage], con.parity))) {
-                ok = false;
-                break;
-            }
-            const int stage = con.stage;
+        if (t == 0)
+            for (int sidx = 0; sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx) issue(sidx);
+        for (int sidx = 0; live_epoch(sidx * H); ++sidx) {
+            if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H)) issue(sidx + FT_NSTAGE - 1);
+            const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
             const float2 *S = strips + con.stage * FT_STRIP - (tmin[sidx * H] & ~1);
             con.next();
 #pragma unroll
@@ -701,21 +651,18 @@ __device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_
                         add2(acc[gg][r], src[dg]);
                 }
             }
-            __syncwarp();
-            if ((t & 31) == 0) mbar_arrive(&sm.empty[stage]);
-        }
-        if (__syncthreads_or(!ok)) {
-            if (t == 0) {
-                atomicExch(status, CETRA_ETIMEOUT);
-                while (con.n < iss.n) {
-                    mbar_wait(&sm.bar[con.stage], con.parity);
-                    con.next();
+            if (__syncthreads_or(!ok)) {
+                if (t == 0) {
+                    atomicExch(status, CETRA_ETIMEOUT);
+                    while (con.n < iss.n) {
+                        mbar_wait(&sm.bar[con.stage], con.parity);
+                        con.next();
+                    }
                 }
+                return false;
             }
-            return false;
         }
-        // every copy is consumed and every warp is past the barrier: the strip ring is free
-        // to hold one period's partial sums
+        // every copy is consumed: the strip ring is free to hold one period's partial sums
         float2 *part = strips;
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg) {
@@ -913,10 +860,7 @@ __device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
 
 __device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
     if (threadIdx.x == 0) {
-        for (int st = 0; st < FT_NSTAGE; ++st) {
-            mbar_init(&sm.bar[st], 1);
-            mbar_init(&sm.empty[st], FT_THREADS / 32);
-        }
+        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
         fence_mbar_init();
     }
     __syncthreads();
