@@ -672,6 +672,13 @@ def main():
                        "unit": "TFLOP/s", "frac": lin_fl / (lin_ms_per * 1e-3) / 1e12 / fma_peak,
                        "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 x {clk:.0f} MHz",
                        "flops_per_launch": lin_fl, "ms_per_launch": lin_ms_per}
+    # the fold's real bound once the grid is L2-resident: shared-memory reads, 128 B/clk/SM
+    smem_peak = sm_count * 128 * clk * 1e6 / 1e9
+    roofline_onchip = {"bound": "shared memory", "kernel": "fold_tma_kernel",
+                       "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                       "frac": achieved / smem_peak,
+                       "peak_source": f"{sm_count} SMs x 128 B/clk x {clk:.0f} MHz",
+                       "note": "every algorithmic cell read is one 8-B shared-memory load"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -688,6 +695,7 @@ def main():
                     "d2h_bytes_per_step": int(d2h),
                     "api": "cetra_linear_search + cetra_periodic_search (host buffers, pinned)"},
             "roofline": roofline, "roofline_linear": roofline_linear,
+            "roofline_onchip": roofline_onchip,
             "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kern.items()},
             "wall_s_timed": wall, "best_period_d": float(w.periods[best]) if best is not None and best >= 0 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
