@@ -63,7 +63,7 @@ def parse():
                          "curves, then search held-out curves with it and with the full fold")
     ap.add_argument("--proposal-train", type=int, default=200000)
     ap.add_argument("--proposal-eval", type=int, default=8192)
-    ap.add_argument("--proposal-epochs", type=int, default=4)
+    ap.add_argument("--proposal-epochs", type=int, default=2)
     ap.add_argument("--proposal-frac", type=float, default=0.05)
     ap.add_argument("--neighbours", action="store_true",
                     help="single-transit search of the 4-yr 1-min curve and the three-round "
