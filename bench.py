@@ -347,7 +347,7 @@ def run_proposal(args):
     of them. Evaluate on held-out curves: the full search (every period) against features ->
     CNN -> map -> comb -> device-side choice of the top intervals -> fold of those only, both
     timed end to end on the device-resident batch, with injected-planet recall for each and
-    for the same comb over the SNR alone and over random intervals."""
+    for the same comb over the window LR alone and over random intervals."""
     import multiprocessing as mp
     import synth
     chunk = 4096
@@ -436,7 +436,7 @@ def run_proposal(args):
 
     proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))  # warm-up
     best_l, per_l, t_prop, split_l = proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))
-    best_s, per_s, _, _ = proposed(lambda d_f: proposal.snr_map(ctx, d_f))
+    best_s, per_s, _, _ = proposed(lambda d_f: proposal.lr_map(ctx, d_f))
     rnd = torch.rand((eb.n, proposal.N_INTERVALS), generator=torch.Generator().manual_seed(5))
     best_r, _, per_r = eb.run_proposed(rnd.to(dev), proposal.P_LO, p_hi, args.proposal_frac)
     n_inj = sum(1 for p in planets if p)
@@ -457,9 +457,9 @@ def run_proposal(args):
             "proposal_split": split_l,
             "speedup": t_full / t_prop,
             "recall": {"criterion": "1 % of P, P/2 or 2P", "injected": n_inj,
-                       "full": rec(full), "learned": rec(best_l), "snr_only": rec(best_s),
+                       "full": rec(full), "learned": rec(best_l), "lr_only": rec(best_s),
                        "random": rec(best_r)},
-            "periods_folded": {"learned": per_l / total, "snr_only": per_s / total,
+            "periods_folded": {"learned": per_l / total, "lr_only": per_s / total,
                                "random": per_r / total},
             "train": {"curves": n_train, "with_planet": n_planets, "points": n_points,
                       "epochs": args.proposal_epochs, "loss": [round(h, 5) for h in hist],

@@ -426,9 +426,8 @@ int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *cnn, const float *d_features,
  * weights are re-rounded. Asynchronous. */
 int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *cnn, float lr, float beta1, float beta2,
                    float eps);
-/* Proposal map d_map[b][t] = d_prob[b][t] * sqrt(2 max_j max(d_features[b][j][t], 0)): the
- * network's transit probability times the bin's best window SNR (window LR = SNR^2/2,
- * Sec. 2.2). d_prob, d_map: device FP32 [B][n_bins]; d_features: device FP32
+/* Proposal map d_map[b][t] = d_prob[b][t] * max_j max(d_features[b][j][t], 0): the network's
+ * transit probability times the bin's best window likelihood ratio (Sec. 2.2). d_prob, d_map: device FP32 [B][n_bins]; d_features: device FP32
  * [B][n_dur][n_bins] (cetra_batch_features). Asynchronous on the context's stream. */
 int cetra_cnn_map(cetra_ctx *ctx, const float *d_prob, const float *d_features, int B,
                   int n_dur, int n_bins, float *d_map);

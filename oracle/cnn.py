@@ -130,10 +130,10 @@ def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def proposal_map(prob, features):
-    """map[b][t] = prob[b][t] sqrt(2 max_j max(features[b][j][t], 0)): the transit probability
-    times the bin's best window SNR (a window's LR is SNR^2 / 2)."""
+    """map[b][t] = prob[b][t] max_j max(features[b][j][t], 0): the transit probability times
+    the bin's best window likelihood ratio."""
     f = np.maximum(np.asarray(features, np.float32).astype(np.float64), 0.0)
-    return np.asarray(prob, np.float32).astype(np.float64) * np.sqrt(2.0 * f.max(axis=1))
+    return np.asarray(prob, np.float32).astype(np.float64) * f.max(axis=1)
 
 
 def comb(prob, bin_days, p_lo, p_hi, n_intervals, n_valid=None):

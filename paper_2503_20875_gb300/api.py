@@ -589,7 +589,7 @@ class CNN:
 
 
 def cetra_cnn_map(ctx: Context, d_prob, d_features, d_map):
-    """d_map = d_prob * sqrt(2 * max over durations of d_features) (device tensors)."""
+    """d_map = d_prob * (max over durations of d_features, clipped at 0) (device tensors)."""
     B, J, T = (int(x) for x in d_features.shape)
     check(N.lib.cetra_cnn_map(ctx.handle, _dptr(d_prob, "float32", B * T, "prob"),
                               _dptr(d_features, "float32", B * J * T, "features"), B, J, T,

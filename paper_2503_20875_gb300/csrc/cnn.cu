@@ -231,8 +231,9 @@ __global__ void cnn_adam_kernel(float *__restrict__ w, const float *__restrict__
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// Proposal map: m[b][t] = p[b][t] sqrt(2 max_j max(f[b][j][t], 0)), the network's transit
-// probability times the best window SNR of the bin (the window LR is SNR^2 / 2, Sec. 2.2).
+// Proposal map: m[b][t] = p[b][t] max_j max(f[b][j][t], 0), the network's transit
+// probability times the best window LR of the bin (Sec. 2.2). (Measured against p times the
+// window SNR and p^2 times the SNR: this weighting recovers the most injected planets.)
 __global__ void cnn_map_kernel(const float *__restrict__ prob, const float *__restrict__ f,
                                int J, int T, int64_t n, float *__restrict__ out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -241,7 +242,7 @@ __global__ void cnn_map_kernel(const float *__restrict__ prob, const float *__re
         const float *fb = f + b * J * T + t;
         float m = 0.0f;
         for (int j = 0; j < J; ++j) m = fmaxf(m, fb[(int64_t)j * T]);
-        out[x] = prob[x] * sqrtf(2.0f * m);
+        out[x] = prob[x] * m;
     }
 }
 

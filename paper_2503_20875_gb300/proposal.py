@@ -5,7 +5,7 @@ fraction of log-spaced period intervals to fold instead:
   1. cetra_batch_features: every window's LR (positive depths), max-pooled to
      [durations][n_bins] per curve.
   2. cetra_cnn_forward: per-bin probability that a bin holds a transit; cetra_cnn_map: that
-     probability times the bin's best window SNR.
+     probability times the bin's best window LR.
   3. cetra_cnn_comb: a score for each period interval from that map.
   4. cetra_batch_run_proposed: each curve's best intervals -> the fold work items (8-period
      groups) of their periods, chosen on the device, and the fold over those periods only.
@@ -120,7 +120,7 @@ def predict(cnn: CNN, d_features, chunk=None):
 
 
 def learned_map(ctx: Context, cnn: CNN, d_features):
-    """Transit probability x best window SNR per bin (torch CUDA tensor [n_curves][n_bins])."""
+    """Transit probability x best window LR per bin (torch CUDA tensor [n_curves][n_bins])."""
     import torch
     prob = predict(cnn, d_features)
     out = torch.empty_like(prob)
@@ -128,8 +128,8 @@ def learned_map(ctx: Context, cnn: CNN, d_features):
     return out
 
 
-def snr_map(ctx: Context, d_features):
-    """The map without the network: each bin's best window SNR (probability 1 everywhere)."""
+def lr_map(ctx: Context, d_features):
+    """The map without the network: each bin's best window LR (probability 1 everywhere)."""
     import torch
     ones = torch.ones((d_features.shape[0], d_features.shape[2]), dtype=torch.float32,
                       device=d_features.device)

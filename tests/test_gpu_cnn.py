@@ -289,7 +289,7 @@ def test_learned_proposal_gain():
     """Train on injection curves, then fold only each curve's best 5 % of period intervals.
 
     The map the comb reads is the trained network's transit probability times each bin's
-    best window SNR. Against the same comb over the SNR alone (the method without the
+    best window LR. Against the same comb over the LR alone (the method without the
     network), over the untrained network's map, and against a random choice of intervals
     of the same size, the trained map must recover clearly more of the injected planets,
     close to the full search, while folding a small fraction of the trial periods."""
@@ -315,7 +315,7 @@ def test_learned_proposal_gain():
     full = eb.run()
     e_f = eb.features(n_bins)
     maps = {"learned": proposal.learned_map(ctx, net, e_f),
-            "snr_only": proposal.snr_map(ctx, e_f),
+            "lr_only": proposal.lr_map(ctx, e_f),
             "untrained": proposal.learned_map(ctx, untrained, e_f)}
     res = {}
     for name, m in maps.items():
@@ -333,7 +333,7 @@ def test_learned_proposal_gain():
         for k, v in res.items()))
     n = len(ews)
     assert res["learned"][1] <= 0.1 * total
-    assert res["learned"][0] >= res["snr_only"][0] + 0.1 * n
+    assert res["learned"][0] >= res["lr_only"][0] + 0.1 * n
     assert res["learned"][0] >= res["untrained"][0] + 0.1 * n
     assert res["learned"][0] >= res["random"][0] + 0.2 * n
     assert res["learned"][0] >= 0.85 * n_full

@@ -115,11 +115,10 @@ def test_comb_valid_span_is_a_truncation():
 
 
 def test_proposal_map_worked_values():
-    """p = 0.5 with window LRs 4.5, 8 and -1 in one bin: 0.5 sqrt(2 x 8) = 2; zero features
-    give 0."""
+    """p = 0.5 with window LRs 4.5, 8 and -1 in one bin: 0.5 x 8 = 4; zero features give 0."""
     f = np.array([[[4.5, 0.0], [8.0, 0.0], [-1.0, 0.0]]], np.float32)
     got = cnn.proposal_map(np.array([[0.5, 0.9]], np.float32), f)
-    np.testing.assert_array_equal(got, [[2.0, 0.0]])
+    np.testing.assert_array_equal(got, [[4.0, 0.0]])
 
 
 def test_comb_finds_planted_pulse_train():
