@@ -404,6 +404,8 @@ int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch,
 void cetra_cnn_destroy(cetra_cnn *cnn);
 /* Number of FP32 parameters (the length of host_params / host_grads below). */
 int64_t cetra_cnn_param_count(const cetra_cnn *cnn);
+/* The sizes a network was created with (each output may be NULL). */
+int cetra_cnn_shape(const cetra_cnn *cnn, int *in_channels, int *n_bins, int *max_batch);
 /* Copy the FP32 training copy of the parameters to host_params (caller-owned). Blocks. */
 int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *cnn, float *host_params);
 /* Replace the parameters from host_params, re-round the BF16 weights and reset the optimiser
@@ -446,6 +448,19 @@ int cetra_cnn_map(cetra_ctx *ctx, const float *d_prob, const float *d_features, 
 int cetra_cnn_comb(cetra_ctx *ctx, const float *d_map, int B, int n_bins,
                    const double *d_bin_days, const int *d_n_valid, double p_lo, double p_hi,
                    int n_intervals, float *d_scores);
+
+/* The whole learned-proposal search of a batch in one call (not in the paper): resample and
+ * linear stages, features (cetra_batch_features at the network's n_bins), the network's
+ * probabilities (in chunks of its max_batch), the map, the comb over n_intervals intervals
+ * between p_lo and p_hi (p_hi <= 0: just above the batch's longest trial period), and
+ * cetra_batch_run_proposed with top_frac. The network must have n_dur input channels. Device
+ * scratch (features, maps, scores: about n_curves x (n_dur + 2) x n_bins x 4 bytes) is allocated
+ * and freed by the call. Outputs as cetra_batch_run_proposed. Blocks.
+ * Errors: CETRA_EINVAL (arguments, channel mismatch), CETRA_ENOMEM, CETRA_ECUDA, CETRA_ETIMEOUT. */
+int cetra_batch_search_proposed(cetra_ctx *ctx, cetra_batch *batch, cetra_cnn *cnn,
+                                int n_intervals, double p_lo, double p_hi, double top_frac,
+                                cetra_best *best, int64_t *n_items_out, int64_t *n_periods_out);
+
 
 /* ---------------------------------------------------------------------------------------
  * Method neighbours of the search.

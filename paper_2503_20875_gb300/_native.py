@@ -139,6 +139,9 @@ SIGNATURES = {
     "cetra_batch_run_proposed": (_INT, [_P, _P, _P, _INT, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, _INT, _P, _P, _P, _P]),
     "cetra_cnn_map": (_INT, [_P, _P, _P, _INT, _INT, _INT, _P]),
+    "cetra_cnn_shape": (_INT, [_P, ctypes.POINTER(_INT), ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
+    "cetra_batch_search_proposed": (_INT, [_P, _P, _P, _INT, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, _P, _P, _P]),
     "cetra_cnn_comb": (_INT, [_P, _P, _INT, _INT, _P, _P, ctypes.c_double, ctypes.c_double, _INT,
                               _P]),
     "cetra_search_batch": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,

@@ -493,6 +493,18 @@ class Batch:
         out = (_best_dict(best), n_it.value, n_per.value)
         return out + (np.sort(buf[:n_it.value]),) if items else out
 
+    def search_proposed(self, cnn, n_intervals=512, p_lo=0.5, p_hi=0.0, top_frac=0.05):
+        """The whole learned-proposal search in one library call (cetra_batch_search_proposed).
+        Returns (best dict, n_items, n_periods)."""
+        best = (N.cetra_best * self.n)()
+        n_it, n_per = ctypes.c_int64(), ctypes.c_int64()
+        check(N.lib.cetra_batch_search_proposed(self.ctx.handle, self.handle, cnn.handle,
+                                                int(n_intervals), float(p_lo), float(p_hi),
+                                                float(top_frac), best, ctypes.byref(n_it),
+                                                ctypes.byref(n_per)),
+              self.ctx.handle, "batch_search_proposed")
+        return _best_dict(best), n_it.value, n_per.value
+
     def close(self):
         if self.handle:
             N.lib.cetra_batch_destroy(self.handle)

@@ -499,6 +499,61 @@ int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *b, const float *d_scor
     return CETRA_OK;
 }
 
+int cetra_batch_search_proposed(cetra_ctx *ctx, cetra_batch *b, cetra_cnn *cnn, int n_intervals,
+                                double p_lo, double p_hi, double top_frac, cetra_best *best,
+                                int64_t *n_items_out, int64_t *n_periods_out) {
+    if (!ctx || !b || !cnn || n_intervals < 1 || n_intervals > SEL_MAX_INTERVALS || !(p_lo > 0.0))
+        return set_error(ctx, CETRA_EINVAL, "batch_search_proposed: bad argument");
+    int cin = 0, T = 0, mb = 0;
+    cetra_cnn_shape(cnn, &cin, &T, &mb);
+    const int J = b->plan->J, n = b->n_curves;
+    if (cin != J) return set_error(ctx, CETRA_EINVAL, "batch_search_proposed: network channels != durations");
+    if (!(p_hi > 0.0)) {  // just above the longest trial period of the batch
+        p_hi = 0.0;
+        for (const auto &cv : b->curves)
+            if (cv.n_periods > 0)
+                p_hi = std::max(p_hi, batch_period_host(cv.pmin, cv.ratio, cv.n_periods - 1));
+        p_hi = p_hi > 0.0 ? p_hi * (1.0 + 1e-9) : 2.0 * p_lo;
+    }
+    // per-curve bin width (days) and valid bins of the features
+    std::vector<double> bw((size_t)n, 0.0);
+    std::vector<int> nv((size_t)n, 0);
+    for (int c = 0; c < n; ++c) {
+        const int64_t I = b->curves[(size_t)c].I;
+        if (I <= 0) continue;
+        const int64_t width = (I + T - 1) / T;
+        bw[(size_t)c] = (double)width * b->plan->t0_step;
+        nv[(size_t)c] = (int)((I + width - 1) / width);
+    }
+    const size_t nf = (size_t)n * J * T, nm = (size_t)n * T, ns = (size_t)n * n_intervals;
+    char *mem = nullptr;
+    const size_t bytes = (nf + 2 * nm + ns) * sizeof(float) + (size_t)n * (sizeof(double) + sizeof(int)) + 1024;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (!e && cudaMalloc((void **)&mem, bytes) != cudaSuccess)
+        return set_error(ctx, CETRA_ENOMEM, "batch_search_proposed: device scratch");
+    float *feat = reinterpret_cast<float *>(mem);
+    float *prob = feat + nf, *map = prob + nm, *scores = map + nm;
+    double *d_bw = reinterpret_cast<double *>(scores + ns);
+    int *d_nv = reinterpret_cast<int *>(d_bw + n);
+    int rc = CETRA_OK;
+    if (!e) e = cudaMemcpyAsync(d_bw, bw.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(d_nv, nv.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    if (e) rc = cuda_fail(ctx, e, "batch_search_proposed");
+    if (rc == CETRA_OK) rc = cetra_batch_features(ctx, b, T, feat);
+    for (int a = 0; rc == CETRA_OK && a < n; a += mb)
+        rc = cetra_cnn_forward(ctx, cnn, feat + (size_t)a * J * T, std::min(mb, n - a),
+                               prob + (size_t)a * T);
+    if (rc == CETRA_OK) rc = cetra_cnn_map(ctx, prob, feat, n, J, T, map);
+    if (rc == CETRA_OK)
+        rc = cetra_cnn_comb(ctx, map, n, T, d_bw, d_nv, p_lo, p_hi, n_intervals, scores);
+    if (rc == CETRA_OK)
+        rc = cetra_batch_run_proposed(ctx, b, scores, n_intervals, p_lo, p_hi, top_frac, 0, best,
+                                      n_items_out, n_periods_out, nullptr);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(mem);
+    return rc;
+}
+
 int cetra_batch_curve(const cetra_batch *b, int curve, double *t_ref, double *period_min,
                       double *period_ratio, int32_t *n_periods, int32_t *n_t0,
                       int64_t *first_item) {

@@ -480,6 +480,14 @@ void cetra_cnn_destroy(cetra_cnn *n) {
 
 int64_t cetra_cnn_param_count(const cetra_cnn *n) { return n ? n->n_params : 0; }
 
+int cetra_cnn_shape(const cetra_cnn *n, int *in_channels, int *n_bins, int *max_batch) {
+    if (!n) return CETRA_EINVAL;
+    if (in_channels) *in_channels = n->cin;
+    if (n_bins) *n_bins = n->T;
+    if (max_batch) *max_batch = n->max_batch;
+    return CETRA_OK;
+}
+
 int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *n, float *host) {
     if (!ctx || !n || !host) return set_error(ctx, CETRA_EINVAL, "cnn_get_params: NULL argument");
     cudaError_t e = cudaMemcpyAsync(host, n->d_params, (size_t)n->n_params * 4,

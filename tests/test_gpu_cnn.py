@@ -278,6 +278,28 @@ def test_run_proposed_matches_oracle_selection():
         b.run_proposed(torch.from_numpy(sc).cuda(), 0.5, 3.0, 0.0)
 
 
+def test_search_proposed_one_call_equals_the_steps():
+    """cetra_batch_search_proposed gives the same best models and fold work as the step by
+    step proposal (features, network, map, comb, device selection and fold)."""
+    torch = _torch()
+    from paper_2503_20875_gb300 import CNN, proposal
+    ctx, b, ws = _batch(20, seed=34, max_sectors=4, ratio=None)
+    net = CNN(ctx, b.info["n_dur"], n_bins=1024, max_batch=8, seed=5)
+    geo = proposal.geometry(b)
+    p_hi = proposal.period_max(geo)
+    one, n_it1, n_per1 = b.search_proposed(net, n_intervals=128, p_lo=0.5, p_hi=p_hi,
+                                           top_frac=0.1)
+    feats = b.features(1024)
+    m = proposal.learned_map(ctx, net, feats)
+    steps, n_it2, n_per2 = proposal.propose_and_fold(ctx, b, m, p_hi, 0.1, n_intervals=128,
+                                                     geo=geo)
+    assert (n_it1, n_per1) == (n_it2, n_per2)
+    for key in ("k", "i", "j", "dlogl", "period", "t0"):
+        np.testing.assert_array_equal(one[key], steps[key])
+    # default upper edge (p_hi <= 0) runs too
+    b.search_proposed(net, n_intervals=64, top_frac=0.2)
+
+
 def _recovered(period, planets):
     if not planets or not np.isfinite(period):
         return False
