@@ -136,6 +136,26 @@ def test_comb_matches_oracle():
     assert np.all(got[4] == 0.0)
 
 
+def test_comb_full_width_matches_oracle():
+    """The comb at the full 4,096-bin width on a learned-map-like input (sparse positive
+    bins), over narrow intervals at short and long periods (cheap for the plain loops)."""
+    torch = _torch()
+    from paper_2503_20875_gb300 import Context, cetra_cnn_comb
+    ctx = Context(0)
+    rng = np.random.default_rng(12)
+    T = 4096
+    m = (rng.uniform(size=(2, T)) ** 8).astype(np.float32)
+    m[0, 100::731] += 3.0  # a pulse train every 731 bins
+    bw = np.array([0.1, 0.013])
+    nv = np.array([4096, 3500], np.int32)
+    for lo, hi, n in ((0.5, 0.5 * 1.004 ** 3, 3), (73.0, 73.3, 2), (150.0, 162.0, 2)):
+        scores = torch.empty((2, n), dtype=torch.float32, device="cuda")
+        cetra_cnn_comb(ctx, torch.from_numpy(m).cuda(), torch.from_numpy(bw).cuda(), lo, hi, n,
+                       scores, torch.from_numpy(nv).cuda())
+        ref = ocnn.comb(m, bw, lo, hi, n, nv)
+        np.testing.assert_allclose(scores.cpu().numpy(), ref, rtol=5e-6, atol=1e-6)
+
+
 def test_comb_large_map_from_global_memory():
     """A map too large for shared memory (32,768 bins) is read from global memory."""
     torch = _torch()
