@@ -87,6 +87,14 @@ def test_iterative_search_matches_oracle():
         assert got["dlogl"][r] == pytest.approx(det["dlogl"], rel=1e-5)
         assert got["depth"][r] == pytest.approx(det["depth"], rel=1e-5)
     assert abs(got["period"][0] - 3.3) < 0.033 and abs(got["period"][1] - 5.7) < 0.057
+    # argument errors are refused before any launch
+    from paper_2503_20875_gb300 import CetraError, cetra_mask_transits
+    for bad in ((0.0, 1.0, 0.1), (float("nan"), 1.0, 0.1), (2.0, float("inf"), 0.1),
+                (2.0, 1.0, -0.1)):
+        with pytest.raises(CetraError):
+            cetra_mask_transits(ctx, grid, *bad)
+    with pytest.raises(CetraError):
+        cetra_search_iterative(ctx, grid, periods, n_iter=0)
 
 
 def _compare_events(got_i, got_j, got_lr, g, d, dep, lr, n_ref_i, n_ref_j):
