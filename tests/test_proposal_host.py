@@ -54,3 +54,16 @@ def test_n_valid_counts_occupied_bins():
             width = max(1, (I + n_bins - 1) // n_bins)
             assert v == len({i // width for i in range(I)})
             assert v <= n_bins
+
+
+def test_packed_batch_generator_matches_the_list_form():
+    """make_batch_csr packs exactly the curves make_batch_workload makes (same seed)."""
+    import synth
+    ws = synth.make_batch_workload(n_curves=5, seed=77, planet_frac=0.5, with_periods=False)
+    off, t, f, e, planets = synth.make_batch_csr((5, 77, 0.5))
+    assert off.tolist() == [0] + np.cumsum([w.time.size for w in ws]).tolist()
+    for c, w in enumerate(ws):
+        np.testing.assert_array_equal(t[off[c]:off[c + 1]], w.time)
+        np.testing.assert_array_equal(f[off[c]:off[c + 1]], w.flux)
+        np.testing.assert_array_equal(e[off[c]:off[c + 1]], w.flux_err)
+        assert planets[c] == w.planets
