@@ -884,7 +884,7 @@ fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
         const int k0 = grp * FT_G;
         __syncthreads();  // the previous group is done with the shared tables
         if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
-        if (!fold_group<KAHAN, KAHAN ? FT_R / 4 : FT_R>(sm, strips, tab, ab, I, ld, J, durations,
+        if (!fold_group<KAHAN, KAHAN ? FT_R / 2 : FT_R>(sm, strips, tab, ab, I, ld, J, durations,
                                                          mask, k0, iss, con, status))
             return;  // uniform: every thread saw the same vote
         for (int g = 0; g < FT_G; ++g) {
@@ -1448,7 +1448,7 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
     if (n_items <= 0) return cudaSuccess;
     auto kern = batch_fold_kernel<false, FT_R>;
     if (plan->precision == CETRA_FP32_KAHAN)
-        kern = batch_fold_kernel<true, FT_R / 4>;
+        kern = batch_fold_kernel<true, FT_R / 2>;
     else if (variant == 1)
         kern = batch_fold_kernel<false, FT_R / 2>;
     kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
@@ -1490,7 +1490,7 @@ cudaError_t batch_configure(const cetra_plan *plan) {
         if (e != cudaSuccess) return e;
     }
     for (auto fn : {batch_fold_kernel<false, FT_R>, batch_fold_kernel<false, FT_R / 2>,
-                    batch_fold_kernel<true, FT_R / 4>}) {
+                    batch_fold_kernel<true, FT_R / 2>}) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)fold_smem_bytes());
         if (e != cudaSuccess) return e;
