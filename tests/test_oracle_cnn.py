@@ -173,3 +173,26 @@ def test_propose_items_everything_and_outside_periods():
     want = np.unique(ok // 8)
     np.testing.assert_array_equal(items, want)
     assert n_per == sum(min(8, 300 - 8 * g) for g in want)
+
+
+def test_comb_rounds_to_the_nearest_bin_and_stops_at_half_the_span():
+    """A pulse train at the nearest bins of a 50.5-bin period (t_e = floor(7 + 50.5 e + 1/2)):
+    with V = 1,050 valid bins the single interval [50, 51) has 21 trials whose 11th is exactly
+    50.5, which hits all 21 pulses: sqrt(21) (truncating the phases would hit every other one).
+    Trials above V/2 are skipped: an interval of periods between V/2 and V scores 0 on a map
+    of ones."""
+    import math
+    V = 1050
+    m = np.zeros((1, V))
+    e = np.arange(21)
+    m[0, np.floor(7 + 50.5 * e + 0.5).astype(int)] = 1.0
+    sc = cnn.comb(m, [1.0], 50.0, 51.0, 1)
+    assert sc[0, 0] == pytest.approx(math.sqrt(21.0), rel=1e-12)
+    ones = np.ones((1, 100))
+    assert cnn.comb(ones, [1.0], 55.0, 95.0, 3).max() == 0.0
+    assert cnn.comb(ones, [1.0], 30.0, 45.0, 1)[0, 0] > 0.0
+    # an interval straddling V/2: the 55-bin period of two pulses (bins 0 and 55) is above
+    # V/2 = 50 and skipped; the trials below it catch one pulse of two epochs: 1/sqrt(2)
+    two = np.zeros((1, 100))
+    two[0, [0, 55]] = 1.0
+    assert cnn.comb(two, [1.0], 45.0, 60.0, 1)[0, 0] == pytest.approx(1 / math.sqrt(2), rel=1e-12)

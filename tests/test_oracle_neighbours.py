@@ -88,10 +88,13 @@ def _sort_and_scan(g, durations, depth, lr, max_events):
     return out
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_monotransits_equal_sort_and_scan(seed):
-    t, f, e, d = _curve(n=600, durations_h=(1.0, 2.5, 5.0))
-    g = oracle.geometry(t, f, e, d, cadence=CAD, t0_step=CAD / 2)
+@pytest.mark.parametrize("seed,durations_h,step", [
+    (0, (1.0, 2.5, 5.0), CAD / 2), (1, (1.0, 2.5, 5.0), CAD / 2), (2, (1.0, 2.5, 5.0), CAD / 2),
+    # durations of exactly 2, 4 and 8 t0 steps: cells exactly one duration away stay visible
+    (3, (0.75, 1.5, 3.0), CAD), (4, (0.75, 1.5, 3.0), CAD)])
+def test_monotransits_equal_sort_and_scan(seed, durations_h, step):
+    t, f, e, d = _curve(n=600, durations_h=durations_h)
+    g = oracle.geometry(t, f, e, d, cadence=CAD, t0_step=step)
     rng = np.random.default_rng(seed)
     J, I = d.size, g.n_t0
     lr = np.round(rng.exponential(3.0, size=(J, I)), 1)  # rounding makes exact ties
