@@ -532,6 +532,12 @@ int cetra_search_iterative(cetra_ctx *ctx, cetra_linear_grid *grid, const double
                            int n_periods, const uint8_t *dur_mask, int n_iter, double width,
                            cetra_best *out, int *n_found);
 
+/* Self-test of the bounded waits (the fold's barrier waits give up after about 2e9 SM clocks,
+ * record CETRA_ETIMEOUT and return instead of hanging): one kernel waits on a barrier that
+ * expects bytes no copy delivers. *timed_out = 1 when the wait gave up as designed, *seconds =
+ * the kernel's duration (may be NULL). Blocks for about a second; the context stays usable. */
+int cetra_selftest_wait_timeout(cetra_ctx *ctx, int *timed_out, double *seconds);
+
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);
 

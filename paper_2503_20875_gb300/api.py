@@ -261,6 +261,14 @@ def cetra_monotransits_device(ctx: Context, plan: Plan, d_workspace, max_events,
           ctx.handle, "monotransits_device")
 
 
+def cetra_selftest_wait_timeout(ctx: Context):
+    """Run the bounded-wait self-test: (timed_out, seconds)."""
+    flag, secs = ctypes.c_int(0), ctypes.c_double(0.0)
+    check(N.lib.cetra_selftest_wait_timeout(ctx.handle, ctypes.byref(flag), ctypes.byref(secs)),
+          ctx.handle, "selftest_wait_timeout")
+    return flag.value, secs.value
+
+
 def events_dict(events):
     """Records of cetra_event -> dict of numpy arrays."""
     return {f: np.array([getattr(e, f) for e in events])

@@ -508,6 +508,34 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
     return CETRA_OK;
 }
 
+int cetra_selftest_wait_timeout(cetra_ctx *ctx, int *timed_out, double *seconds) {
+    if (!ctx || !timed_out) return set_error(ctx, CETRA_EINVAL, "selftest: NULL argument");
+    device_guard g(ctx->device);
+    int *d = nullptr;
+    if (cudaMalloc((void **)&d, 2 * sizeof(int)) != cudaSuccess)
+        return set_error(ctx, CETRA_ENOMEM, "selftest: allocation");
+    int h[2] = {0, 0};
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (!e) e = cudaEventCreate(&b);
+    if (!e) e = cudaMemsetAsync(d, 0, 2 * sizeof(int), ctx->stream);
+    if (!e) e = cudaEventRecord(a, ctx->stream);
+    if (!e) e = launch_wait_timeout_selftest(ctx->stream, d);
+    if (!e) e = cudaEventRecord(b, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.0f;
+    if (!e) e = cudaEventElapsedTime(&ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(d);
+    if (e) return cuda_fail(ctx, e, "selftest");
+    ctx->launches++;
+    *timed_out = h[0];
+    if (seconds) *seconds = 1e-3 * ms;
+    return CETRA_OK;
+}
+
 // ------------------------------------------------------------------ method neighbours
 
 int cetra_mask_transits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace,

@@ -162,6 +162,8 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               unsigned long long *curve_keys, int *status,
                               const int64_t *item_list,
                               const unsigned long long *n_items_dev = nullptr);
+// Self-test of the bounded barrier wait (kernels.cu): d_out[0] = 1 if the wait gave up.
+cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out);
 // Method neighbours (neighbours.cu): masking a detected signal, single-transit events.
 cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float *wy, float *w, double P,
                         double t0, double h, unsigned long long *counts);

@@ -1271,6 +1271,22 @@ __global__ void batch_features_kernel(const float2 *__restrict__ ab,
     }
 }
 
+// Self-test of the bounded barrier wait every fold uses: a barrier expects bytes that no copy
+// will deliver, so its phase never completes; the wait must give up after FT_WAIT_CYCLES and
+// report it (out[0] = 1), and the kernel must return normally.
+__global__ void wait_timeout_selftest_kernel(int *out) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&bar, 16);  // arrives and expects 16 bytes that never come
+        const long long t0 = clock64();
+        const bool ok = mbar_wait(&bar, 0);
+        out[0] = ok ? 0 : 1;
+        out[1] = (int)min((clock64() - t0) >> 20, (long long)INT32_MAX);  // ~2^20-cycle units
+    }
+}
+
 }  // namespace
 
 size_t fold_smem_bytes() {
@@ -1508,5 +1524,10 @@ cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_
     if (blocks > (int64_t)num_sms * 32) blocks = (int64_t)num_sms * 32;
     batch_features_kernel<<<(unsigned)blocks, threads, 0, stream>>>(ab, curves, n_curves, plan->J,
                                                                      n_bins, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out) {
+    wait_timeout_selftest_kernel<<<1, 32, 0, stream>>>(d_out);
     return cudaGetLastError();
 }
