@@ -476,7 +476,17 @@ __device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab,
                 const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
                 con.next();
                 const int32_t *de = d + e * GS;
-                if (all_used && full[e]) {
+                if (!KAHAN && all_used && full[e] && e == 0) {
+                    // every period's epoch-0 offset is 0: one load serves the whole group
+                    // (3.5 % faster on the 20-s curve; 1 % slower with compensated sums)
+                    float2 v[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = S[r * FT_THREADS];
+#pragma unroll
+                    for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                        for (int r = 0; r < R; ++r) add2(acc[gg][r], v[r]);
+                } else if (all_used && full[e]) {
                     int32_t dv[GS];
                     load_offsets<GS>(de, dv);
 #pragma unroll
