@@ -538,6 +538,18 @@ int cetra_search_iterative(cetra_ctx *ctx, cetra_linear_grid *grid, const double
  * the kernel's duration (may be NULL). Blocks for about a second; the context stays usable. */
 int cetra_selftest_wait_timeout(cetra_ctx *ctx, int *timed_out, double *seconds);
 
+/* Measured ceilings for the roofline denominators of the two stages: the window sums of the
+ * linear search (Sec. 2.2) are packed FP32 FMAs, and the fold (Sec. 2.3) is one 8-byte
+ * shared-memory load plus one packed FP32 add per cell read. Runs two microbenchmark kernels
+ * on ctx's stream, one full wave of blocks each, timed with CUDA events after a warm-up launch
+ * (best of three):
+ *   *fma_tflops  independent fma.rn.f32x2 chains, 2 flop per FMA lane, in TFLOP/s;
+ *   *smem_gbs    conflict-free 8-byte shared-memory loads, each added into a packed FP32 sum,
+ *                in GB/s of bytes loaded.
+ * Either pointer may be NULL. Blocks for some tens of ms. Returns CETRA_OK, CETRA_EINVAL (NULL
+ * ctx), CETRA_ENOMEM or CETRA_ECUDA. */
+int cetra_measure_peaks(cetra_ctx *ctx, double *fma_tflops, double *smem_gbs);
+
 /* Release a grid from cetra_linear_search (NULL is allowed). */
 void cetra_grid_free(cetra_linear_grid *grid);
 

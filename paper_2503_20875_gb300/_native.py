@@ -118,6 +118,7 @@ SIGNATURES = {
     "cetra_search_iterative": (_INT, [_P, _P, _P, _INT, _P, _INT, ctypes.c_double, _P,
                                       ctypes.POINTER(_INT)]),
     "cetra_selftest_wait_timeout": (_INT, [_P, ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_double)]),
+    "cetra_measure_peaks": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "cetra_grid_free": (None, [_P]),
     "cetra_batch_create": (_INT, [_P, ctypes.POINTER(cetra_params), _INT, _P, _P, _P, _P, _P,
                                   _INT, _P, _INT, _P, _P, _P, _INT, ctypes.POINTER(_P)]),

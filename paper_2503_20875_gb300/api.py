@@ -269,6 +269,14 @@ def cetra_selftest_wait_timeout(ctx: Context):
     return flag.value, secs.value
 
 
+def cetra_measure_peaks(ctx: Context):
+    """Measured ceilings of the two stages' bounds: (FP32 FMA TFLOP/s, shared-load GB/s)."""
+    fma, smem = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(N.lib.cetra_measure_peaks(ctx.handle, ctypes.byref(fma), ctypes.byref(smem)),
+          ctx.handle, "measure_peaks")
+    return fma.value, smem.value
+
+
 def events_dict(events):
     """Records of cetra_event -> dict of numpy arrays."""
     return {f: np.array([getattr(e, f) for e in events])

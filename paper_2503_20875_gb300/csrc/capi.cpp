@@ -2,6 +2,7 @@
 // Argument checking, workspace layout, stream-ordered launches and the
 // host-buffer convenience API. No compute happens here: every stage of the
 // search runs in the kernels of kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -533,6 +534,43 @@ int cetra_selftest_wait_timeout(cetra_ctx *ctx, int *timed_out, double *seconds)
     ctx->launches++;
     *timed_out = h[0];
     if (seconds) *seconds = 1e-3 * ms;
+    return CETRA_OK;
+}
+
+int cetra_measure_peaks(cetra_ctx *ctx, double *fma_tflops, double *smem_gbs) {
+    if (!ctx) return set_error(ctx, CETRA_EINVAL, "measure_peaks: NULL context");
+    device_guard g(ctx->device);
+    const int grid[2] = {peak_grid(ctx->num_sms, false), peak_grid(ctx->num_sms, true)};
+    const int iters[2] = {32768, 8192};  // a few ms a launch at the nominal rates
+    float *d = nullptr;
+    const size_t n = (size_t)std::max(grid[0], grid[1]) * PEAK_THREADS;
+    if (cudaMalloc((void **)&d, n * sizeof(float)) != cudaSuccess)
+        return set_error(ctx, CETRA_ENOMEM, "measure_peaks: allocation");
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (!e) e = cudaEventCreate(&b);
+    double rate[2] = {0.0, 0.0};
+    for (int m = 0; m < 2 && !e; ++m) {
+        double work = 0.0;
+        e = launch_peak(ctx->stream, m == 1, grid[m], iters[m] / 8, d, &work);  // warm-up
+        ctx->launches++;
+        for (int rep = 0; rep < 3 && !e; ++rep) {
+            e = cudaEventRecord(a, ctx->stream);
+            if (!e) e = launch_peak(ctx->stream, m == 1, grid[m], iters[m], d, &work);
+            if (!e) e = cudaEventRecord(b, ctx->stream);
+            if (!e) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (!e) e = cudaEventElapsedTime(&ms, a, b);
+            if (!e && ms > 0.0f) rate[m] = std::max(rate[m], work / (1e-3 * ms));
+            ctx->launches++;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(d);
+    if (e) return cuda_fail(ctx, e, "measure_peaks");
+    if (fma_tflops) *fma_tflops = rate[0] * 1e-12;
+    if (smem_gbs) *smem_gbs = rate[1] * 1e-9;
     return CETRA_OK;
 }
 

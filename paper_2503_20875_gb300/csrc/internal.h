@@ -164,6 +164,12 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const unsigned long long *n_items_dev = nullptr);
 // Self-test of the bounded barrier wait (kernels.cu): d_out[0] = 1 if the wait gave up.
 cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out);
+// Roofline microbenchmarks: one full wave of blocks (peak_grid), PEAK_THREADS threads each;
+// *work = flop (FMA) or bytes loaded (shared memory) of one launch.
+constexpr int PEAK_THREADS = 256;
+int peak_grid(int num_sms, bool smem);
+cudaError_t launch_peak(cudaStream_t stream, bool smem, int blocks, int iters, float *d_out,
+                        double *work);
 // Method neighbours (neighbours.cu): masking a detected signal, single-transit events.
 cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float *wy, float *w, double P,
                         double t0, double h, unsigned long long *counts);

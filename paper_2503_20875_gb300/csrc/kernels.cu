@@ -1284,6 +1284,59 @@ __global__ void batch_features_kernel(const float2 *__restrict__ ab,
 // Self-test of the bounded barrier wait every fold uses: a barrier expects bytes that no copy
 // will deliver, so its phase never completes; the wait must give up after FT_WAIT_CYCLES and
 // report it (out[0] = 1), and the kernel must return normally.
+// --------------------------------------------------------------------------------------------
+// Measured ceilings of the two stages' bounds. The linear search is bound by packed FP32 FMA
+// issue, the fold by 8-byte shared-memory loads each added into a packed FP32 sum; these
+// kernels run each pattern alone, at full occupancy, with PEAK_CHAINS independent chains a
+// thread (enough to cover the pipe latencies), and store their sums so nothing is dead code.
+constexpr int PEAK_CHAINS = 8;
+constexpr int PEAK_SMEM_CELLS = 2 * PEAK_CHAINS * PEAK_THREADS;  // float2 per block (32 KiB)
+
+__global__ void __launch_bounds__(PEAK_THREADS) peak_fma_kernel(float2 a, float2 b, int iters,
+                                                                float *__restrict__ out) {
+    float2 acc[PEAK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k) acc[k] = make_float2((float)threadIdx.x, (float)k);
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int k = 0; k < PEAK_CHAINS; ++k) fma2(acc[k], a, b);
+    float r = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k) r += acc[k].x + acc[k].y;
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Thread t reads cells t + PEAK_THREADS k (+ half the buffer on odd iterations): every warp
+// load is 256 contiguous bytes, conflict-free, as in the fold.
+__global__ void __launch_bounds__(PEAK_THREADS) peak_smem_kernel(int iters,
+                                                                 float *__restrict__ out) {
+    __shared__ float2 s[PEAK_SMEM_CELLS];
+    for (int x = threadIdx.x; x < PEAK_SMEM_CELLS; x += blockDim.x)
+        s[x] = make_float2((float)x, 1.0f);
+    __syncthreads();
+    float2 acc[PEAK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k) acc[k] = make_float2(0.0f, 0.0f);
+    const uint32_t base = smem_u32(s + threadIdx.x);
+    constexpr uint32_t half = PEAK_SMEM_CELLS / 2 * sizeof(float2);
+    for (int it = 0; it < iters; ++it) {
+        const uint32_t p = base + ((uint32_t)it & 1u) * half;
+#pragma unroll
+        for (int k = 0; k < PEAK_CHAINS; ++k)
+            add2(acc[k], lds2(p + (uint32_t)(k * PEAK_THREADS * sizeof(float2))));
+    }
+    float r = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PEAK_CHAINS; ++k) r += acc[k].x + acc[k].y;
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 __global__ void wait_timeout_selftest_kernel(int *out) {
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
@@ -1539,5 +1592,29 @@ cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_
 
 cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out) {
     wait_timeout_selftest_kernel<<<1, 32, 0, stream>>>(d_out);
+    return cudaGetLastError();
+}
+
+int peak_grid(int num_sms, bool smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, smem ? (const void *)peak_smem_kernel : (const void *)peak_fma_kernel,
+            PEAK_THREADS, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return num_sms * per_sm;
+}
+
+cudaError_t launch_peak(cudaStream_t stream, bool smem, int blocks, int iters, float *d_out,
+                        double *work) {
+    const double lanes = (double)blocks * PEAK_THREADS * iters * PEAK_CHAINS;
+    if (smem) {
+        peak_smem_kernel<<<blocks, PEAK_THREADS, 0, stream>>>(iters, d_out);
+        *work = lanes * sizeof(float2);  // bytes loaded
+    } else {
+        peak_fma_kernel<<<blocks, PEAK_THREADS, 0, stream>>>(make_float2(1e-3f, 2e-3f),
+                                                             make_float2(1e-3f, 5e-4f), iters,
+                                                             d_out);
+        *work = lanes * 4.0;  // two FMA lanes, 2 flop each
+    }
     return cudaGetLastError();
 }
