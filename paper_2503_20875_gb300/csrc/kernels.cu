@@ -1306,9 +1306,11 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_fma_kernel(float2 a, float2
     out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// A volatile load: the buffer is never written in the loop, and a plain load could be lifted
+// out of it, leaving only the adds to time.
 __device__ __forceinline__ float2 lds2(uint32_t addr) {
     float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
     return v;
 }
 

@@ -16,6 +16,8 @@ def test_measured_peaks_within_nominal():
     ghz = 2.2  # above any GB300 SM clock
     fma_nominal = sms * 128 * 2 * ghz * 1e-3         # TFLOP/s
     smem_nominal = sms * 128 * ghz                   # GB/s at 128 B/clk/SM
-    assert math.isfinite(fma) and 0.3 * fma_nominal < fma <= fma_nominal
-    assert math.isfinite(smem) and 0.1 * smem_nominal < smem <= 2.0 * smem_nominal
-    print(f"FP32 FMA {fma:.1f} TFLOP/s, shared loads {smem:.0f} GB/s")
+    msg = f"FP32 FMA {fma:.1f} TFLOP/s, shared loads {smem:.0f} GB/s"
+    print(msg)
+    assert math.isfinite(fma) and 0.3 * fma_nominal < fma <= fma_nominal, msg
+    # above the nominal rate would mean loads were lifted out of the timed loop
+    assert math.isfinite(smem) and 0.1 * smem_nominal < smem <= smem_nominal, msg
