@@ -389,10 +389,13 @@ int cetra_linear_search(cetra_ctx *ctx, const cetra_params *params, const double
     double *d_t = static_cast<double *>(d_in);
     float *d_f = reinterpret_cast<float *>(static_cast<char *>(d_in) + nb_t);
     float *d_e = d_f + n_points;
-    cudaMemcpyAsync(d_t, time, nb_t, cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(d_f, flux, nb_f, cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemcpyAsync(d_e, flux_err, nb_f, cudaMemcpyHostToDevice, ctx->stream);
-    rc = cetra_resample_device(ctx, plan, d_t, d_f, d_e, n_points, grid->d_work, grid->work_bytes);
+    cudaError_t ce = cudaMemcpyAsync(d_t, time, nb_t, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_f, flux, nb_f, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_e, flux_err, nb_f, cudaMemcpyHostToDevice, ctx->stream);
+    rc = ce != cudaSuccess ? cuda_fail(ctx, ce, "linear_search: input copy")
+                           : cetra_resample_device(ctx, plan, d_t, d_f, d_e, n_points,
+                                                   grid->d_work, grid->work_bytes);
     float *d_out = nullptr;
     const size_t cells = (size_t)plan->J * (size_t)I;
     int nout = (depth ? 1 : 0) + (depth_var ? 1 : 0) + (dlogl ? 1 : 0);
@@ -409,9 +412,12 @@ int cetra_linear_search(cetra_ctx *ctx, const cetra_params *params, const double
         float *dl = dlogl ? o : nullptr;
         rc = cetra_linear_device(ctx, plan, grid->d_work, grid->work_bytes, dd, dv, dl);
         if (rc == CETRA_OK) {
-            if (depth) cudaMemcpyAsync(depth, dd, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
-            if (depth_var) cudaMemcpyAsync(depth_var, dv, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
-            if (dlogl) cudaMemcpyAsync(dlogl, dl, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (depth) ce = cudaMemcpyAsync(depth, dd, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (depth_var && ce == cudaSuccess)
+                ce = cudaMemcpyAsync(depth_var, dv, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (dlogl && ce == cudaSuccess)
+                ce = cudaMemcpyAsync(dlogl, dl, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+            if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "linear_search: output copy");
         }
     }
     e = cudaStreamSynchronize(ctx->stream);
@@ -470,11 +476,15 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
     double *d_P = reinterpret_cast<double *>(d_buf);
     double *d_out = d_P + K;  // 5 K doubles
     uint8_t *d_mask = dur_mask ? reinterpret_cast<uint8_t *>(d_out + 5 * K) : nullptr;
-    cudaMemcpyAsync(d_P, periods, K * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-    if (dur_mask) cudaMemcpyAsync(d_mask, dur_mask, K * J, cudaMemcpyHostToDevice, ctx->stream);
-    int rc = cetra_periodic_device(ctx, plan, grid->d_work, grid->work_bytes, d_P, n_periods,
-                                   d_mask, d_out, d_out + K, d_out + 2 * K, d_out + 3 * K,
-                                   d_out + 4 * K, nullptr, nullptr);
+    cudaError_t ce = cudaMemcpyAsync(d_P, periods, K * sizeof(double), cudaMemcpyHostToDevice,
+                                     ctx->stream);
+    if (dur_mask && ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_mask, dur_mask, K * J, cudaMemcpyHostToDevice, ctx->stream);
+    int rc = ce != cudaSuccess
+                 ? cuda_fail(ctx, ce, "periodic_search: input copy")
+                 : cetra_periodic_device(ctx, plan, grid->d_work, grid->work_bytes, d_P,
+                                         n_periods, d_mask, d_out, d_out + K, d_out + 2 * K,
+                                         d_out + 3 * K, d_out + 4 * K, nullptr, nullptr);
     double *h_lr = dlogl;
     std::vector<double> tmp;
     if (!h_lr && best_k) {
@@ -482,11 +492,12 @@ int cetra_periodic_search(cetra_ctx *ctx, cetra_linear_grid *grid, const double 
         h_lr = tmp.data();
     }
     if (rc == CETRA_OK) {
-        if (h_lr) cudaMemcpyAsync(h_lr, d_out, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
-        if (t0) cudaMemcpyAsync(t0, d_out + K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
-        if (duration) cudaMemcpyAsync(duration, d_out + 2 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
-        if (depth) cudaMemcpyAsync(depth, d_out + 3 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
-        if (depth_var) cudaMemcpyAsync(depth_var, d_out + 4 * K, K * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        double *dst[5] = {h_lr, t0, duration, depth, depth_var};
+        for (int m = 0; m < 5 && ce == cudaSuccess; ++m)
+            if (dst[m])
+                ce = cudaMemcpyAsync(dst[m], d_out + m * K, K * 8, cudaMemcpyDeviceToHost,
+                                     ctx->stream);
+        if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "periodic_search: output copy");
     }
     e = cudaStreamSynchronize(ctx->stream);
     cudaFree(d_buf);
