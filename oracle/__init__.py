@@ -14,7 +14,8 @@ Parity status: every step is pinned by the CPU tests in
 ``tests/test_oracle_pins.py`` (closed forms, noiseless injections, brute-force
 likelihood maximisation, invariants, the paper's toy example); the only
 conventions that no external fact fixes are the readings R1, R3, R5, R6 and R7
-listed in the C file, which are choices rather than results.
+listed in the C file, which are choices rather than results (parity unpinned for
+those conventions only).
 """
 from __future__ import annotations
 

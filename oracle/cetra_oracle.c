@@ -53,6 +53,10 @@
  *       duration of that event's mid-time (|i - i_e| < D_e q / (c p), FP64);
  *       ties go to the smallest j, then the smallest i.
  *
+ * Parity unpinned: R1, R3, R5, R6 and R7 are conventions that no external fact
+ * fixes (the GPU path takes the same ones); every computation around them is
+ * pinned by the CPU tests against closed forms, brute force and invariants.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (R8 needs
  * -ffp-contract=off: aarch64 compilers contract a*b+c into fma by default).
  */
