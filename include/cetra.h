@@ -88,6 +88,8 @@ void cetra_params_default(cetra_params *p);
  * Errors: CETRA_EINVAL (ctx NULL), CETRA_ECUDA (bad device).
  */
 int cetra_create(cetra_ctx **ctx, int device, void *cuda_stream);
+/* Release a context. The objects made with it (plans, grids, batches, networks) may be
+ * released before or after it, but none may be used once it is gone. */
 void cetra_destroy(cetra_ctx *ctx);
 /* Change the stream of a context (e.g. to a torch stream). */
 int cetra_set_stream(cetra_ctx *ctx, void *cuda_stream);

@@ -18,7 +18,8 @@
 #include "internal.h"
 
 struct cetra_batch {
-    cetra_ctx *ctx = nullptr;
+    cetra_ctx *ctx = nullptr;    // used while the batch runs, never by its destruction
+    int device = 0;
     cetra_plan *plan = nullptr;  // shared geometry constants and window tables
     int n_curves = 0;
     std::vector<batch_curve> curves;
@@ -230,6 +231,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     cetra_batch *b = new (std::nothrow) cetra_batch;
     if (!b) return fail(ctx, CETRA_ENOMEM, "batch: host allocation");
     b->ctx = ctx;
+    b->device = ctx->device;
     b->n_curves = n_curves;
     b->n_points = n_points;
     auto bail = [&](int rc) {
@@ -593,7 +595,7 @@ int cetra_batch_get_info(const cetra_batch *b, cetra_batch_info *info) {
 
 void cetra_batch_destroy(cetra_batch *b) {
     if (!b) return;
-    cudaSetDevice(b->ctx->device);
+    cudaSetDevice(b->device);
     release(b);
 }
 

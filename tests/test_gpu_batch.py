@@ -114,6 +114,31 @@ def test_batch_edge_cases():
               t0_step=STEP)
 
 
+def test_objects_released_after_their_context():
+    """A batch, a grid and a plan may be released after the context that made them."""
+    from paper_2503_20875_gb300 import Context, Batch, Plan, cetra_linear_search
+    ws, curves = _curves(2, seed=6)
+    ctx = Context(0)
+    b = Batch(ctx, curves, ws[0].durations, ws[0].template, 0.5, None, 1.004, cadence=CAD,
+              t0_step=STEP)
+    got = b.run()
+    assert got["k"].shape == (2,)
+    grid, _, _, _ = cetra_linear_search(ctx, ws[0].time, ws[0].flux, ws[0].flux_err,
+                                        ws[0].durations, ws[0].template, outputs=False,
+                                        cadence=CAD, t0_step=STEP)
+    plan = Plan(ctx, ws[0].time, ws[0].flux, ws[0].flux_err, ws[0].durations, ws[0].template,
+                cadence=CAD, t0_step=STEP)
+    ctx.close()
+    b.close()
+    grid.close()
+    plan.close()
+    # the device is still usable by a new context
+    ctx2 = Context(0)
+    again = Batch(ctx2, curves, ws[0].durations, ws[0].template, 0.5, None, 1.004, cadence=CAD,
+                  t0_step=STEP).run()
+    np.testing.assert_array_equal(again["k"], got["k"])
+
+
 def test_batch_recovery_equals_plain_form():
     """Injection-recovery (period within 1 % of P, P/2 or 2P; Sec. 3.1) of the batched
     form equals the plain per-curve GPU form on the same curves (both find the same
