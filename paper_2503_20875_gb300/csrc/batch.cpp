@@ -331,7 +331,8 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_items = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1) * sizeof(int64_t));
     o_flags = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1));
     o_cnt = off; off = up(off + 2 * sizeof(unsigned long long));
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (e) return bail(cuda_fail(ctx, e, "batch device"));
     e = cudaMalloc(&b->d_mem, off);
     if (e) {
@@ -385,7 +386,8 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
 
 int cetra_batch_run(cetra_ctx *ctx, cetra_batch *b, cetra_best *best) {
     if (!ctx || !b) return set_error(ctx, CETRA_EINVAL, "batch_run: NULL argument");
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (e) return cuda_fail(ctx, e, "batch_run device");
     if (!b->graph) {
         cudaGraph_t g = nullptr;
@@ -422,7 +424,8 @@ int cetra_batch_run(cetra_ctx *ctx, cetra_batch *b, cetra_best *best) {
 int cetra_batch_features(cetra_ctx *ctx, cetra_batch *b, int n_bins, float *d_features) {
     if (!ctx || !b || !d_features || n_bins < 1)
         return set_error(ctx, CETRA_EINVAL, "batch_features: bad argument");
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
     if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
     if (!e) e = enqueue_linear(b, b->lin_threads);
@@ -443,7 +446,8 @@ int cetra_batch_run_items(cetra_ctx *ctx, cetra_batch *b, const int64_t *items, 
     for (int64_t x = 0; x < n_items; ++x)
         if (items[x] < 0 || items[x] >= b->n_items)
             return set_error(ctx, CETRA_EINVAL, "batch_run_items: item out of range");
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
     if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
     if (!e && n_items)
@@ -471,7 +475,8 @@ int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *b, const float *d_scor
         !(p_lo > 0.0) || !(p_hi > p_lo) || !std::isfinite(p_hi) || !(top_frac > 0.0) ||
         !(top_frac <= 1.0))
         return set_error(ctx, CETRA_EINVAL, "batch_run_proposed: bad argument");
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = cudaEventRecord(b->ev_start, ctx->stream);
     if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_start, 0);
     if (!e && linear) e = enqueue_linear(b, b->lin_threads);
@@ -530,7 +535,8 @@ int cetra_batch_search_proposed(cetra_ctx *ctx, cetra_batch *b, cetra_cnn *cnn, 
     const size_t nf = (size_t)n * J * T, nm = (size_t)n * T, ns = (size_t)n * n_intervals;
     char *mem = nullptr;
     const size_t bytes = (nf + 2 * nm + ns) * sizeof(float) + (size_t)n * (sizeof(double) + sizeof(int)) + 1024;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e && cudaMalloc((void **)&mem, bytes) != cudaSuccess)
         return set_error(ctx, CETRA_ENOMEM, "batch_search_proposed: device scratch");
     float *feat = reinterpret_cast<float *>(mem);
@@ -595,7 +601,7 @@ int cetra_batch_get_info(const cetra_batch *b, cetra_batch_info *info) {
 
 void cetra_batch_destroy(cetra_batch *b) {
     if (!b) return;
-    cudaSetDevice(b->device);
+    device_guard dguard(b->device);
     release(b);
 }
 

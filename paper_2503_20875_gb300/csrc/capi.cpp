@@ -52,18 +52,6 @@ int cuda_fail(cetra_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, CETRA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-struct device_guard {
-    int prev = -1;
-    explicit device_guard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~device_guard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 // The three device regions of a workspace.
 struct ws_ptrs {
     float *wy, *w;

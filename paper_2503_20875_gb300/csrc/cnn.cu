@@ -334,6 +334,7 @@ unsigned grid_for(int64_t n, int threads, int num_sms) {
 // ------------------------------------------------------------------------------- host side
 
 struct cetra_cnn {
+    int device = 0;
     int cin = 0, T = 0, max_batch = 0;
     int ch_in[CNN_LAYERS], ch_out[CNN_LAYERS];
     int64_t w_off[CNN_LAYERS], b_off[CNN_LAYERS], n_params = 0;
@@ -404,6 +405,7 @@ int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch,
                          "cnn_create: need 1 <= in_channels <= 32, n_bins a multiple of 256, max_batch >= 1");
     cetra_cnn *n = new (std::nothrow) cetra_cnn;
     if (!n) return set_error(ctx, CETRA_ENOMEM, "cnn_create: host allocation");
+    n->device = ctx->device;
     n->cin = in_channels;
     n->T = n_bins;
     n->max_batch = max_batch;
@@ -430,7 +432,8 @@ int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch,
     const size_t act = (size_t)max_batch * CNN_C * n_bins;
     const size_t bytes = P * sizeof(float) * 4 + P * sizeof(__nv_bfloat16) * 2 + 256 * 8 +
                          act * sizeof(float) * (CNN_LAYERS + 1 + 2) + 1024;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = cudaMalloc(&n->d_mem, bytes);
     if (e) {
         delete n;
@@ -474,6 +477,7 @@ int cetra_cnn_create(cetra_ctx *ctx, int in_channels, int n_bins, int max_batch,
 
 void cetra_cnn_destroy(cetra_cnn *n) {
     if (!n) return;
+    device_guard dguard(n->device);
     cudaFree(n->d_mem);
     delete n;
 }
@@ -490,7 +494,9 @@ int cetra_cnn_shape(const cetra_cnn *n, int *in_channels, int *n_bins, int *max_
 
 int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *n, float *host) {
     if (!ctx || !n || !host) return set_error(ctx, CETRA_EINVAL, "cnn_get_params: NULL argument");
-    cudaError_t e = cudaMemcpyAsync(host, n->d_params, (size_t)n->n_params * 4,
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
+    if (!e) e = cudaMemcpyAsync(host, n->d_params, (size_t)n->n_params * 4,
                                     cudaMemcpyDeviceToHost, ctx->stream);
     if (!e) e = cudaStreamSynchronize(ctx->stream);
     return e ? cnn_fail(ctx, e, "cnn_get_params") : CETRA_OK;
@@ -498,7 +504,9 @@ int cetra_cnn_get_params(cetra_ctx *ctx, const cetra_cnn *n, float *host) {
 
 int cetra_cnn_set_params(cetra_ctx *ctx, cetra_cnn *n, const float *host) {
     if (!ctx || !n || !host) return set_error(ctx, CETRA_EINVAL, "cnn_set_params: NULL argument");
-    cudaError_t e = cudaMemcpyAsync(n->d_params, host, (size_t)n->n_params * 4,
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
+    if (!e) e = cudaMemcpyAsync(n->d_params, host, (size_t)n->n_params * 4,
                                     cudaMemcpyHostToDevice, ctx->stream);
     if (!e) e = round_weights(ctx, n);
     // new parameters start a new optimisation: clear Adam's moments and step count
@@ -513,7 +521,8 @@ int cetra_cnn_forward(cetra_ctx *ctx, cetra_cnn *n, const float *d_features, int
                       float *d_prob) {
     if (!ctx || !n || !d_features || !d_prob || B < 1 || B > n->max_batch)
         return set_error(ctx, CETRA_EINVAL, "cnn_forward: bad argument");
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = forward(ctx, n, d_features, B);
     if (!e) {
         const int64_t m = (int64_t)B * n->T;
@@ -531,7 +540,8 @@ int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *n, const float *d_features,
     if (!ctx || !n || !d_features || !d_labels || B < 1 || B > n->max_batch)
         return set_error(ctx, CETRA_EINVAL, "cnn_backward: bad argument");
     const int T = n->T;
-    cudaError_t e = cudaSetDevice(ctx->device);
+    device_guard dguard(ctx->device);
+    cudaError_t e = dguard.status;
     if (!e) e = forward(ctx, n, d_features, B);
     if (!e) e = cudaMemsetAsync(n->d_grads, 0, (size_t)n->n_params * 4, ctx->stream);
     if (!e) e = cudaMemsetAsync(n->d_loss, 0, sizeof(double), ctx->stream);
@@ -577,6 +587,8 @@ int cetra_cnn_backward(cetra_ctx *ctx, cetra_cnn *n, const float *d_features,
 
 int cetra_cnn_adam(cetra_ctx *ctx, cetra_cnn *n, float lr, float beta1, float beta2, float eps) {
     if (!ctx || !n) return set_error(ctx, CETRA_EINVAL, "cnn_adam: NULL argument");
+    device_guard dguard(ctx->device);
+    if (dguard.status) return cnn_fail(ctx, dguard.status, "cnn_adam");
     n->adam_step++;
     const float c1 = 1.0f - std::pow(beta1, (float)n->adam_step);
     const float c2 = 1.0f - std::pow(beta2, (float)n->adam_step);
@@ -592,6 +604,8 @@ int cetra_cnn_map(cetra_ctx *ctx, const float *d_prob, const float *d_features, 
                   int n_dur, int n_bins, float *d_map) {
     if (!ctx || !d_prob || !d_features || !d_map || B < 1 || n_dur < 1 || n_bins < 1)
         return set_error(ctx, CETRA_EINVAL, "cnn_map: bad argument");
+    device_guard dguard(ctx->device);
+    if (dguard.status) return cnn_fail(ctx, dguard.status, "cnn_map");
     const int64_t n = (int64_t)B * n_bins;
     cnn_map_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, ctx->stream>>>(d_prob, d_features,
                                                                            n_dur, n_bins, n, d_map);
@@ -606,6 +620,8 @@ int cetra_cnn_comb(cetra_ctx *ctx, const float *d_prob, int B, int n_bins,
     if (!ctx || !d_prob || !d_bin_days || !d_scores || B < 1 || B > 65535 || n_bins < 1 ||
         n_bins > (1 << 30) || n_intervals < 1 || !(p_lo > 0.0) || !(p_hi > p_lo))
         return set_error(ctx, CETRA_EINVAL, "cnn_comb: bad argument");
+    device_guard dguard(ctx->device);
+    if (dguard.status) return cnn_fail(ctx, dguard.status, "cnn_comb");
     dim3 grid((unsigned)n_intervals, (unsigned)B);
     const size_t smem = (size_t)n_bins * sizeof(float);
     cudaError_t e = cudaSuccess;

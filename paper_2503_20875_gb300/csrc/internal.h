@@ -15,6 +15,23 @@
 enum kernel_id { KID_RESAMPLE = 0, KID_LINEAR, KID_FOLD, KID_FINALIZE, KID_LOGL0, KID_COUNT };
 extern const char *const kernel_names[KID_COUNT];
 
+// Makes `dev` the calling thread's current device for the guard's scope and restores the
+// caller's device afterwards; `status` is the result of switching.
+struct device_guard {
+    int prev = -1;
+    cudaError_t status = cudaSuccess;
+    explicit device_guard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) status = cudaSetDevice(dev);
+    }
+    ~device_guard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    device_guard(const device_guard &) = delete;
+    device_guard &operator=(const device_guard &) = delete;
+};
+
 struct cetra_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -51,18 +51,6 @@ int scratch_address(cetra_ctx *ctx, void **out) {
     return CETRA_OK;
 }
 
-struct current_device {
-    int prev = -1;
-    explicit current_device(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~current_device() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 }  // namespace
 
 extern "C" int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *plan,
@@ -87,7 +75,7 @@ extern "C" int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *pl
     const ws_layout L = workspace_layout(plan, 0);
     if (workspace_bytes < L.total)
         return set_error(ctx, CETRA_ECAPACITY, "periodic_device_static: workspace too small");
-    current_device guard(ctx->device);
+    device_guard guard(ctx->device);
     void *scratch = nullptr;
     int rc = scratch_address(ctx, &scratch);
     if (rc != CETRA_OK) return rc;
