@@ -36,6 +36,26 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= set(N.SIGNATURES), set(names) - set(N.SIGNATURES)
 
 
+def test_header_is_plain_c(tmp_path):
+    """A C99 translation unit that includes the header and takes the address of every
+    declared entry point compiles without a warning (the boundary needs no C++)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = _declared()
+    src = ['#include "cetra.h"', "#include <stddef.h>", "typedef void (*entry)(void);",
+           "static const entry table[] = {"]
+    src += [f"    (entry)&{n}," for n in names]
+    src += ["    NULL};", "int main(void) { return table[0] == NULL; }"]
+    c = tmp_path / "consumer.c"
+    c.write_text("\n".join(src) + "\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(c),
+                        "-o", str(tmp_path / "consumer.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def _geom_lib(t, f, e, durs, cadence=0.0, t0_step=0.0):
     from paper_2503_20875_gb300 import _native as N
     from paper_2503_20875_gb300.api import make_params, _ptr
