@@ -11,6 +11,12 @@ periods 0.5-13.5 d (synthetic, seeded).
          between steps by a 256 MiB write outside the timed events)
   e2e    the host-buffer C-ABI calls (cetra_linear_search +
          cetra_periodic_search) from pinned host memory, copies included
+  roofline          the fold's algorithmic (A, B) reads against the measured HBM
+         copy peak (above 1: the grid is reused on chip), with its DRAM traffic
+  roofline_onchip   the same rate against the shared-memory load bound
+  roofline_linear   the linear kernel's FP32 FMA rate against the FMA peak
+         (both carry the library's own measured ceilings: peak_measured)
+  cpu_baseline      the FP64 CPU oracle on a bounded sample of the step
   --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
          of each step, extrapolated to curves/s)
 
