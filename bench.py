@@ -11,14 +11,19 @@ periods 0.5-13.5 d (synthetic, seeded).
          between steps by a 256 MiB write outside the timed events)
   e2e    the host-buffer C-ABI calls (cetra_linear_search +
          cetra_periodic_search) from pinned host memory, copies included
-  roofline          the fold's algorithmic (A, B) reads against the measured HBM
-         copy peak (above 1: the grid is reused on chip), with its DRAM traffic
-  roofline_onchip   the same rate against the shared-memory load bound
+  roofline          the fold (the dominant kernel) against its binding bound:
+         every algorithmic cell read is one 8-B shared-memory load, so the
+         shared-memory load bandwidth (SMs x 128 B/clk x clock) is the ceiling
+         while the (A, B) grid stays in L2; hbm_frac = its DRAM traffic (ncu,
+         per launch) over the launch time against the measured HBM copy peak,
+         the binding bound when that fraction is the larger one
   roofline_linear   the linear kernel's FP32 FMA rate against the FMA peak
          (both carry the library's own measured ceilings: peak_measured)
   cpu_baseline      the FP64 CPU oracle on a bounded sample of the step
-  --impl reference   the FP64 CPU oracle on the host cores (a bounded sample
-         of each step, extrapolated to curves/s)
+  --impl reference   the FP64 CPU oracle on the host cores: each step is one
+         bounded sample (the whole linear search + the fold on every n-th
+         period); ms_per_step is that sample's measured time, value the
+         curves/s extrapolated from it (key extrapolated_ms_per_curve)
 
 Multi-GPU: one process per GPU (torchrun); each rank searches its own curves
 (replicas, no collective on the data path); value = all ranks' curves / max
@@ -42,9 +47,9 @@ sys.path.insert(0, ROOT)
 METRIC = "light curves searched/s on 1 GB300 vs plain form; % FMA/HBM peak; ΔlogL rel err"
 UNIT = "curves/s"
 FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one fold launch (ncu capture of this kernel
-# version); None once the kernel changes
-FOLD_DRAM_BYTES = {"tess_20s_27d": 20283392}
+# dram__bytes_read.sum + dram__bytes_write.sum of one full fold launch per workload (one ncu
+# capture of the current fold kernel; an entry is removed whenever the kernel changes)
+FOLD_DRAM_BYTES = {}
 
 
 def parse():
@@ -205,6 +210,9 @@ def cpu_baseline(w, stride, durations=None):
 
 
 def run_reference(args):
+    """The oracle as the reference arm. One step = one bounded sample of the workload (the
+    whole linear search + the fold on every n-th period); ms_per_step is the measured time of
+    a step, and value the curves/s extrapolated from it (the fold scales with the periods)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -213,17 +221,21 @@ def run_reference(args):
     stride = max(1, args.cpu_fold_stride * 4)
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; warm-up steps are not repeated on the CPU
-    vals = []
+    vals, step_s = [], []
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
+        ts = time.perf_counter()
         last = cpu_baseline(w, stride)
+        step_s.append(time.perf_counter() - ts)
         vals.append(1.0 / last["value"])
     wall = time.perf_counter() - t0
     per_curve = sum(vals) / len(vals)
     value = 1.0 / per_curve
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_curve * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(step_s) / len(step_s),
+            "extrapolated_ms_per_curve": per_curve * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_points": int(w.time.size),
@@ -317,7 +329,9 @@ def run_batch(args):
     value = len(ws) / run_s
     achieved = 8.0 * info["fold_cell_reads"] / run_s / 1e9
     peaks = load_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = (peaks or {}).get("sm_max_mhz", 2070.0)
+    peak = sm_count * 128 * clk * 1e6 / 1e9  # shared-memory loads: 128 B/clk/SM
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * run_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -332,9 +346,11 @@ def run_batch(args):
             "e2e": {"value": len(ws) / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(w.time.nbytes + w.flux.nbytes + w.flux_err.nbytes for w in ws)),
                     "d2h_bytes_per_step": 64 * len(ws), "api": "cetra_search_batch"},
-            "roofline": {"bound": "hbm", "kernel": "batch run (fold dominated)",
+            "roofline": {"bound": "smem", "kernel": "batch run (fold dominated)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{sm_count} SMs x 128 B/clk x {clk:.0f} MHz "
+                                        "(shared-memory loads; whole run time)",
                          "cell_reads_per_step": info["fold_cell_reads"]},
             "plain_form": {"curves": m, "value": 1.0 / plain_s, "unit": UNIT,
                            "same_best_period": same},
@@ -658,39 +674,41 @@ def main():
     cells = fold_cells(info, w.durations, w.periods)
     fold_bytes = 8.0 * cells
     achieved = fold_bytes / (fold_ms_per * 1e-3) / 1e9
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    # DRAM bytes of one full fold launch of this workload (ncu, profiles/fold_tma_kernel_tess_20s_27d.md)
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = (peaks or {}).get("sm_max_mhz", 2070.0)
+    # every algorithmic cell read is one 8-B shared-memory load: 128 B/clk/SM
+    smem_peak = sm_count * 128 * clk * 1e6 / 1e9
+    # DRAM bytes of one full fold launch of this workload (one ncu capture of this kernel)
     traffic = (FOLD_DRAM_BYTES.get(args.workload)
                if not args.period_range and args.precision == "fp32" else None)
-    roofline = {"bound": "hbm", "kernel": "fold_tma_kernel", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+    hbm_achieved = traffic / (fold_ms_per * 1e-3) / 1e9 if traffic else None
+    hbm_frac = hbm_achieved / hbm_peak if traffic else None
+    smem_frac = achieved / smem_peak
+    roofline = {"bound": "smem", "kernel": "fold_tma_kernel", "achieved": achieved,
+                "peak": smem_peak, "unit": "GB/s", "frac": smem_frac, "traffic": traffic,
+                "peak_source": f"{sm_count} SMs x 128 B/clk x {clk:.0f} MHz (shared-memory loads)",
+                "hbm_achieved": hbm_achieved, "hbm_peak": hbm_peak, "hbm_frac": hbm_frac,
+                "hbm_peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "algorithmic_bytes_per_launch": fold_bytes, "cell_reads_per_launch": cells,
                 "ms_per_launch": fold_ms_per}
+    if hbm_frac is not None and hbm_frac > smem_frac:
+        roofline.update(bound="hbm", achieved=hbm_achieved, peak=hbm_peak, frac=hbm_frac)
     n_lin, lin_ms = kern["linear"]
     lin_ms_per = lin_ms / max(n_lin, 1)
     lin_fl = 4.0 * sum(info_table_work(plan))
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk = (peaks or {}).get("sm_max_mhz", 2070.0)
     fma_peak = sm_count * 128 * 2 * clk * 1e6 / 1e12
     roofline_linear = {"bound": "alu", "kernel": "linear_kernel<9>",
                        "achieved": lin_fl / (lin_ms_per * 1e-3) / 1e12, "peak": fma_peak,
                        "unit": "TFLOP/s", "frac": lin_fl / (lin_ms_per * 1e-3) / 1e12 / fma_peak,
                        "peak_source": f"{sm_count} SMs x 128 FP32 FMA/clk x 2 x {clk:.0f} MHz",
                        "flops_per_launch": lin_fl, "ms_per_launch": lin_ms_per}
-    # the fold's real bound once the grid is L2-resident: shared-memory reads, 128 B/clk/SM
-    smem_peak = sm_count * 128 * clk * 1e6 / 1e9
-    roofline_onchip = {"bound": "shared memory", "kernel": "fold_tma_kernel",
-                       "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                       "frac": achieved / smem_peak,
-                       "peak_source": f"{sm_count} SMs x 128 B/clk x {clk:.0f} MHz",
-                       "note": "every algorithmic cell read is one 8-B shared-memory load"}
     # the same two bounds measured by the library's own microbenchmarks (after the timed region)
     fma_meas, smem_meas = cetra.cetra_measure_peaks(ctx)
     roofline_linear.update(peak_measured=fma_meas, frac_of_measured=roofline_linear["achieved"] / fma_meas,
                            peak_measured_source="cetra_measure_peaks: packed FP32 FMA chains")
-    roofline_onchip.update(peak_measured=smem_meas, frac_of_measured=achieved / smem_meas,
-                           peak_measured_source="cetra_measure_peaks: 8-B shared loads + packed adds")
+    roofline.update(smem_peak_measured=smem_meas, smem_frac_of_measured=achieved / smem_meas,
+                    smem_peak_measured_source="cetra_measure_peaks: 8-B shared loads + packed adds")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -707,7 +725,6 @@ def main():
                     "d2h_bytes_per_step": int(d2h),
                     "api": "cetra_linear_search + cetra_periodic_search (host buffers, pinned)"},
             "roofline": roofline, "roofline_linear": roofline_linear,
-            "roofline_onchip": roofline_onchip,
             "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kern.items()},
             "wall_s_timed": wall, "best_period_d": float(w.periods[best]) if best is not None and best >= 0 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

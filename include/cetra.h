@@ -204,12 +204,14 @@ int cetra_periodic_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_worksp
  * instead of in d_workspace, so d_workspace needs only
  * cetra_workspace_bytes(plan, 0) bytes and must hold a linear grid from
  * cetra_linear_device. Arguments, outputs and tie rules are those of
- * cetra_periodic_device. The call allocates nothing; its first call on a
- * device looks up the array's device address (make that first call before
- * any stream capture). Calls on one device share the array: calls whose
+ * cetra_periodic_device. The call allocates nothing. Every call looks up the
+ * array's device address with the context's device current (no allocation);
+ * the first call on a device may load the library's device code, so make it
+ * before any stream capture. Calls on one device share the array: calls whose
  * kernels overlap on the GPU race and must be serialised by the caller. The
- * status word is cleared at the start of every call; read it back with a
- * stream synchronisation if needed (a timed-out fold leaves NaN outputs).
+ * status word is cleared at the start of every call; a fold whose bounded
+ * device-side wait gave up sets it to CETRA_ETIMEOUT and leaves NaN outputs
+ * (and indices -1) for every period. Read it with cetra_static_status.
  * Errors: CETRA_ECAPACITY (n_periods > CETRA_STATIC_MAX_PERIODS, or the
  * workspace is smaller than the linear grid), CETRA_EINVAL, CETRA_ECUDA.
  */
@@ -219,6 +221,25 @@ int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *plan, void *d
                                  const uint8_t *d_mask, double *d_dlogl, double *d_t0,
                                  double *d_duration, double *d_depth, double *d_depth_var,
                                  int64_t *d_i, int32_t *d_j);
+
+/*
+ * Status word of the static array after cetra_periodic_device_static on ctx's device: 0, or
+ * CETRA_ETIMEOUT if a bounded device-side wait of that call's fold gave up (its outputs are
+ * then NaN). Waits for ctx's stream, then copies the word to *status; allocates nothing.
+ * The word belongs to the last call on this device from any context.
+ * Errors: CETRA_EINVAL (NULL argument), CETRA_ECUDA.
+ */
+int cetra_static_status(cetra_ctx *ctx, int *status);
+
+/*
+ * Self-test of the allocation-free path's failure report (not in the paper): clears the
+ * static status word of ctx's device, then queues on ctx's stream one kernel whose bounded
+ * barrier wait cannot complete; when the wait gives up (after about a second) the kernel
+ * stores CETRA_ETIMEOUT in the static status word, exactly as a fold whose wait gave up
+ * does. cetra_static_status then reports it; the next cetra_periodic_device_static clears it.
+ * Returns after queueing. Errors: CETRA_EINVAL (NULL ctx), CETRA_ECUDA.
+ */
+int cetra_selftest_static_timeout(cetra_ctx *ctx);
 
 /*
  * Status word of a workspace after cetra_periodic_device: 0, or CETRA_ETIMEOUT

@@ -20,6 +20,7 @@ CETRA_ETIMEOUT = 4
 CETRA_ECAPACITY = 5
 CETRA_FP32 = 0
 CETRA_FP32_KAHAN = 1
+CETRA_STATIC_MAX_PERIODS = 262144  # periods the allocation-free entry point accepts
 
 STATUS_NAMES = {0: "CETRA_OK", 1: "CETRA_EINVAL", 2: "CETRA_ENOMEM", 3: "CETRA_ECUDA",
                 4: "CETRA_ETIMEOUT", 5: "CETRA_ECAPACITY"}
@@ -103,6 +104,8 @@ SIGNATURES = {
     "cetra_workspace_status": (_INT, [_P, _P, _P, _SZ, ctypes.POINTER(_INT)]),
     "cetra_periodic_device_static": (_INT, [_P, _P, _P, _SZ, _P, _INT, _P, _P, _P, _P, _P, _P,
                                             _P, _P]),
+    "cetra_static_status": (_INT, [_P, ctypes.POINTER(_INT)]),
+    "cetra_selftest_static_timeout": (_INT, [_P]),
     "cetra_linear_search": (_INT, [_P, ctypes.POINTER(cetra_params), _P, _P, _P, _I64, _P, _INT,
                                    _P, _INT, ctypes.POINTER(_P), _P, _P, _P,
                                    ctypes.POINTER(_I64)]),

@@ -179,8 +179,10 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               unsigned long long *curve_keys, int *status,
                               const int64_t *item_list,
                               const unsigned long long *n_items_dev = nullptr);
-// Self-test of the bounded barrier wait (kernels.cu): d_out[0] = 1 if the wait gave up.
-cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out);
+// Self-test of the bounded barrier wait (kernels.cu): d_out[0] = 1 if the wait gave up,
+// d_out[1] its duration in units of 2^20 SM clocks (d_out may be NULL); a wait that gave up
+// also stores CETRA_ETIMEOUT in *d_status, as the fold does (d_status may be NULL).
+cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out, int *d_status = nullptr);
 // Roofline microbenchmarks: one full wave of blocks (peak_grid), PEAK_THREADS threads each;
 // *work = flop (FMA) or bytes loaded (shared memory) of one launch.
 constexpr int PEAK_THREADS = 256;

@@ -1339,7 +1339,7 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_smem_kernel(int iters,
     out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
-__global__ void wait_timeout_selftest_kernel(int *out) {
+__global__ void wait_timeout_selftest_kernel(int *out, int *status) {
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -1347,8 +1347,12 @@ __global__ void wait_timeout_selftest_kernel(int *out) {
         mbar_expect_tx(&bar, 16);  // arrives and expects 16 bytes that never come
         const long long t0 = clock64();
         const bool ok = mbar_wait(&bar, 0);
-        out[0] = ok ? 0 : 1;
-        out[1] = (int)min((clock64() - t0) >> 20, (long long)INT32_MAX);  // ~2^20-cycle units
+        // a wait that gave up is recorded the way the fold records it
+        if (!ok && status) atomicExch(status, CETRA_ETIMEOUT);
+        if (out) {
+            out[0] = ok ? 0 : 1;
+            out[1] = (int)min((clock64() - t0) >> 20, (long long)INT32_MAX);  // ~2^20-cycle units
+        }
     }
 }
 
@@ -1592,8 +1596,8 @@ cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_
     return cudaGetLastError();
 }
 
-cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out) {
-    wait_timeout_selftest_kernel<<<1, 32, 0, stream>>>(d_out);
+cudaError_t launch_wait_timeout_selftest(cudaStream_t stream, int *d_out, int *d_status) {
+    wait_timeout_selftest_kernel<<<1, 32, 0, stream>>>(d_out, d_status);
     return cudaGetLastError();
 }
 

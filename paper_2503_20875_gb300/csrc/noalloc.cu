@@ -16,9 +16,13 @@
 // exits. All calls on one device share it: calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on it and must be
 // serialised by the caller. Each call clears the status word before its fold
-// runs; the keys need no clearing because the fold writes every key it reads.
-#include <mutex>
-
+// runs. The keys are not cleared: every block of a fold that completes writes the
+// keys of all its periods before the finalize kernel reads them, and a block whose
+// bounded wait gives up stops without writing its keys but first records
+// CETRA_ETIMEOUT in the status word. The finalize kernel reads the status word
+// first and writes NaN for every period when it is non-zero, so keys left over
+// from an earlier call are never used. cetra_static_status reads the status word
+// back.
 #include "internal.h"
 
 namespace {
@@ -29,25 +33,18 @@ constexpr size_t kKeysBytes = (size_t)kStaticMaxPeriods * sizeof(unsigned long l
 // Keys of the fold (one per period), then the status word at kKeysBytes.
 static __device__ __align__(256) unsigned char g_fold_scratch[kKeysBytes + 256];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {};  // device address of g_fold_scratch, per device
-
 // The host-side name g_fold_scratch is only a stand-in for the symbol: its device
-// address must be looked up once per device, with that device current.
-int scratch_address(cetra_ctx *ctx, void **out) {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    void *&slot = g_scratch_addr[ctx->device];
-    if (!slot) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_fold_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(ctx, CETRA_ECUDA,
-                             std::string("periodic_device_static: scratch address: ") +
-                                 cudaGetErrorString(e));
-        slot = p;
-    }
-    *out = slot;
+// address is looked up with the context's device current. The lookup is repeated on
+// every call (it allocates nothing), so an address never outlives the device context
+// it belongs to (a cudaDeviceReset by the host application re-creates it).
+int scratch_address(cetra_ctx *ctx, const char *who, unsigned long long **keys, int **status) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fold_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(ctx, CETRA_ECUDA,
+                         std::string(who) + ": scratch address: " + cudaGetErrorString(e));
+    *keys = static_cast<unsigned long long *>(p);
+    *status = reinterpret_cast<int *>(static_cast<char *>(p) + kKeysBytes);
     return CETRA_OK;
 }
 
@@ -61,8 +58,6 @@ extern "C" int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *pl
                                             double *d_depth_var, int64_t *d_i, int32_t *d_j) {
     if (!ctx || !plan || !d_workspace)
         return set_error(ctx, CETRA_EINVAL, "periodic_device_static: NULL argument");
-    if (ctx->device < 0 || ctx->device >= kMaxDevices)
-        return set_error(ctx, CETRA_EINVAL, "periodic_device_static: device index out of range");
     if (n_periods < 0)
         return set_error(ctx, CETRA_EINVAL, "periodic_device_static: n_periods < 0");
     if (n_periods > kStaticMaxPeriods)
@@ -76,11 +71,13 @@ extern "C" int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *pl
     if (workspace_bytes < L.total)
         return set_error(ctx, CETRA_ECAPACITY, "periodic_device_static: workspace too small");
     device_guard guard(ctx->device);
-    void *scratch = nullptr;
-    int rc = scratch_address(ctx, &scratch);
+    if (guard.status != cudaSuccess)
+        return set_error(ctx, CETRA_ECUDA, std::string("periodic_device_static: device: ") +
+                                               cudaGetErrorString(guard.status));
+    unsigned long long *keys = nullptr;
+    int *status = nullptr;
+    int rc = scratch_address(ctx, "periodic_device_static", &keys, &status);
     if (rc != CETRA_OK) return rc;
-    unsigned long long *keys = static_cast<unsigned long long *>(scratch);
-    int *status = reinterpret_cast<int *>(static_cast<char *>(scratch) + kKeysBytes);
     const float2 *ab = reinterpret_cast<const float2 *>(static_cast<char *>(d_workspace) + L.ab);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess)
@@ -95,5 +92,44 @@ extern "C" int cetra_periodic_device_static(cetra_ctx *ctx, const cetra_plan *pl
     if (e != cudaSuccess)
         return set_error(ctx, CETRA_ECUDA, std::string("periodic_device_static: finalize launch: ") +
                                                cudaGetErrorString(e));
+    return CETRA_OK;
+}
+
+extern "C" int cetra_static_status(cetra_ctx *ctx, int *status) {
+    if (!ctx || !status) return set_error(ctx, CETRA_EINVAL, "static_status: NULL argument");
+    device_guard guard(ctx->device);
+    if (guard.status != cudaSuccess)
+        return set_error(ctx, CETRA_ECUDA,
+                         std::string("static_status: device: ") + cudaGetErrorString(guard.status));
+    unsigned long long *keys = nullptr;
+    int *d_status = nullptr;
+    int rc = scratch_address(ctx, "static_status", &keys, &d_status);
+    if (rc != CETRA_OK) return rc;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return set_error(ctx, CETRA_ECUDA,
+                         std::string("static_status: read: ") + cudaGetErrorString(e));
+    *status = h;
+    return CETRA_OK;
+}
+
+extern "C" int cetra_selftest_static_timeout(cetra_ctx *ctx) {
+    if (!ctx) return set_error(ctx, CETRA_EINVAL, "selftest_static_timeout: NULL context");
+    device_guard guard(ctx->device);
+    if (guard.status != cudaSuccess)
+        return set_error(ctx, CETRA_ECUDA, std::string("selftest_static_timeout: device: ") +
+                                               cudaGetErrorString(guard.status));
+    unsigned long long *keys = nullptr;
+    int *status = nullptr;
+    int rc = scratch_address(ctx, "selftest_static_timeout", &keys, &status);
+    if (rc != CETRA_OK) return rc;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_wait_timeout_selftest(ctx->stream, nullptr, status);
+    if (e != cudaSuccess)
+        return set_error(ctx, CETRA_ECUDA,
+                         std::string("selftest_static_timeout: ") + cudaGetErrorString(e));
+    ctx->launches++;
     return CETRA_OK;
 }

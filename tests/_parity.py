@@ -13,8 +13,9 @@ Tolerances (FP32 kernels against the FP64 oracle):
   periodic, per period: the argmax (i, j) is identical, unless the oracle's
   own LR at the GPU's argmax is within r_flat of the oracle's maximum (an
   epsilon-tie between windows, reported); LR, depth and var_Z within r_flat
-  relative where LR_o >= 25 and within r_low below that; t0 and duration exact
-  at identical indices.
+  relative where LR_o >= 25 and within r_low below that (r_low = r_flat by
+  default: the flat bound holds at every per-period winner); t0 and duration
+  exact at identical indices.
 Null cells and null periods must coincide exactly.
 """
 from __future__ import annotations
@@ -108,9 +109,11 @@ def compare_linear(gpu, orc, durations, r=1e-6, r_flat=1e-5, lr_sig=25.0, rows=N
     return stats
 
 
-def compare_periodic(gpu, orc, periods, r_flat=1e-5, r_low=1e-4, lr_sig=25.0, lin=None):
+def compare_periodic(gpu, orc, periods, r_flat=1e-5, r_low=None, lr_sig=25.0, lin=None):
     """Per-period comparison. ``lin`` = (depth, var, lr) oracle arrays used for
     epsilon-tie evaluation (defaults to the oracle's full linear arrays)."""
+    if r_low is None:
+        r_low = r_flat
     gp, op = gpu["periodic"], orc["periodic"]
     null_o = np.isnan(op["dlogl"])
     null_g = np.isnan(gp["dlogl"])
@@ -139,11 +142,16 @@ def compare_periodic(gpu, orc, periods, r_flat=1e-5, r_low=1e-4, lr_sig=25.0, li
              "max_rel_depth_sig": float(np.max(rel(gp["depth"][sig], op["depth"][sig]), initial=0)),
              "max_rel_var_sig": float(np.max(rel(gp["depth_var"][sig], op["depth_var"][sig]),
                                              initial=0)),
-             "max_rel_lr_low": float(np.max(rel(gp["dlogl"][low], op["dlogl"][low]), initial=0))}
+             "max_rel_lr_low": float(np.max(rel(gp["dlogl"][low], op["dlogl"][low]), initial=0)),
+             "max_rel_depth_low": float(np.max(rel(gp["depth"][low], op["depth"][low]), initial=0)),
+             "max_rel_var_low": float(np.max(rel(gp["depth_var"][low], op["depth_var"][low]),
+                                             initial=0))}
     assert stats["max_rel_lr_sig"] <= r_flat, stats
     assert stats["max_rel_depth_sig"] <= r_flat, stats
     assert stats["max_rel_var_sig"] <= r_flat, stats
     assert stats["max_rel_lr_low"] <= r_low, stats
+    assert stats["max_rel_depth_low"] <= r_low, stats
+    assert stats["max_rel_var_low"] <= r_low, stats
     np.testing.assert_array_equal(gp["duration"][m], op["duration"][m])
     np.testing.assert_allclose(gp["t0"][m], op["t0"][m], rtol=0, atol=1e-9 * max(1.0, np.nanmax(np.abs(op["t0"]))))
     # the global best period

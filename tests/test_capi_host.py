@@ -135,3 +135,11 @@ def test_binding_refuses_host_and_short_buffers():
     with pytest.raises(ValueError):
         api._dptr(None, "float32", 4, "x")
     assert api._dptr(None, "float32", 4, "x", optional=True) is None
+
+
+def test_static_limit_matches_header():
+    """The binding's CETRA_STATIC_MAX_PERIODS is the header's."""
+    from paper_2503_20875_gb300 import _native as N
+    src = open(os.path.join(ROOT, "include", "cetra.h")).read()
+    m = re.search(r"#define\s+CETRA_STATIC_MAX_PERIODS\s+(\d+)", src)
+    assert m and int(m.group(1)) == N.CETRA_STATIC_MAX_PERIODS
