@@ -1,8 +1,9 @@
 """Build the in-tree CUDA library ``libcetra.so`` for sm_103a (nvcc + g++, no cmake).
 
-Six translation units compiled in parallel and linked into one shared
+The translation units compiled in parallel and linked into one shared
 library next to this file:
-  csrc/kernels.cu  device kernels and their launchers  (nvcc, sm_103a)
+  csrc/kernels.cu  resample, linear, finalize and batch kernels (nvcc, sm_103a)
+  csrc/fold.cu     the periodic-search fold kernels and launchers (nvcc, sm_103a)
   csrc/plan.cpp    host planner, FP64 index arithmetic  (g++, -ffp-contract=off)
   csrc/capi.cpp    the C ABI declared in include/cetra.h (g++)
   csrc/noalloc.cu  the allocation-free periodic entry point (nvcc)
@@ -25,7 +26,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu",
+SOURCES = ["kernels.cu", "fold.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu",
            "neighbours.cu"]
 
 

@@ -1,0 +1,887 @@
+// Sec. 2.3 periodic search on sm_103a: the fold of the linear grid over trial periods with a
+// common depth (Eq. 3, Eq. 4) and the in-kernel maximum per period.
+//
+// With A = sum m W y and B = sum m^2 W per window (Sec. 2.2), Eq. 4 at the common depth
+// Z = sum_e A_e / sum_e B_e is (sum_e A_e)^2 / (2 sum_e B_e), so the fold only sums (A, B)
+// pairs over the epoch cells i + o_e, o_e = floor(e P / s + 1/2) (the nearest t0 point of
+// epoch e, FP64). A null window is (0, 0) and drops out of the sums.
+//
+// Work: one block per group of FT_G neighbouring trial periods (and, for grids larger than
+// the L2, per duration). Neighbouring periods read nearly the same cells, so for a tile of
+// T phases and an epoch e the block copies the union of the cells its periods need,
+// [i0 + min_g o_e(g), i0 + max_g o_e(g) + T), into shared memory with one bulk copy and every
+// period reads its cells from there.
+//
+// Block: FT_THREADS consumer threads and one producer warp. The producer issues the bulk
+// copies into a ring of FT_NSTAGE strips; each strip has a "full" barrier (completed by the
+// copy's byte count) and an "empty" barrier (completed when every consumer thread has read
+// it). Consumers wait only for the strip they read next, so there is no block-wide barrier
+// per epoch; warps drift freely and the shared-memory pipe stays busy. Consumer thread c owns
+// phases i0 + c + r FT_THREADS (r < R) of every period of the sub-group being folded and
+// keeps their (A, B) sums in registers: one 8-byte shared load and one packed FP32 add per
+// cell read.
+//
+// Epoch table: per sub-group the epoch offsets are computed once in FP64 into shared memory
+// as u16 byte offsets of each period's first cell within the epoch's strip, plus the
+// smallest and largest offset of the epoch (the strip's extent). Groups whose table does not
+// fit, or whose offsets spread wider than a strip allows, are split 8 -> 4 -> 2 -> 1; a single
+// period whose table does not fit is folded straight from global memory. Periods with few
+// phases (at most T/2) fold several epochs per strip (epoch slices).
+//
+// Bounded waits: every barrier wait gives up after FT_WAIT_CYCLES; the thread records
+// CETRA_ETIMEOUT in the status word and raises the block's abort flag, after which no thread
+// waits or issues a copy any more: every thread runs on through the same loops and block
+// barriers without work (no thread leaves early, so every block barrier completes), the
+// producer waits (bounded) for the copies it still has in flight, and the block exits. The
+// finalize kernel then writes NaN for every period.
+#include <cfloat>
+#include <cstdint>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace {
+
+// 8-byte shared-memory load at a 32-bit shared address.
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Block-wide barrier that threads may reach from different call sites (the producer warp and
+// the consumer warps run different loops; the non-aligned form allows that).
+__device__ __forceinline__ void block_sync() { asm volatile("barrier.sync 0;" ::: "memory"); }
+
+// One arrival on a barrier (release of this thread's earlier shared-memory reads).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The epoch-0 cell of every period is its phase cell (o_0 = 0), so epoch 0 is shared.
+// Candidate test of the epilogue: 2 LR = x^2 / y exceeds the running best b only if
+// (x (1 + 2^-15)) x > b y. The exact comparison (x * __fdividef(x, y) > b) has a relative
+// error below 2^-21 and each product here one rounding, so the test never rejects a window
+// the exact comparison would take; the exact comparison then decides, as before.
+constexpr float kCandidate = 1.0f + 1.0f / 32768.0f;
+
+// Shared state of a fold block.
+struct fold_smem {
+    uint64_t full[FT_NSTAGE];        // strip landed: the producer's arrival + the copy's bytes
+    uint64_t empty[FT_NSTAGE];       // strip read: one arrival per consumer thread
+    unsigned long long best[FT_G];   // best key of each slot of the group
+    double P[FT_G], Ps[FT_G];        // period (days) and period in t0 steps
+    int nph[FT_G], E[FT_G];          // phases, and an upper bound on the epochs with o_e < I
+    int bad, tight;                  // table votes: spread too wide for the main / sliced path
+    int abort;                       // a bounded wait gave up: no more waits or copies
+};
+
+// Copies issued (producer) or consumed (consumers): copy n uses strip n % FT_NSTAGE and
+// completes phase n / FT_NSTAGE of that strip's barriers.
+struct ring {
+    uint32_t n = 0, stage = 0, parity = 0;
+    __device__ __forceinline__ void next() {
+        ++n;
+        if (++stage == FT_NSTAGE) {
+            stage = 0;
+            parity ^= 1u;
+        }
+    }
+};
+
+// Epoch table of a sub-group of GS periods, Es epochs:
+//   off[e][gg]  u16 byte offset of period gg's first cell o_e within strip e, whose first
+//               cell is (tmin[e] & ~1) (copies start on a 16-byte boundary);
+//   tmin[e], tmax[e]  smallest and largest o_e over the sub-group's present periods.
+struct fold_table {
+    const uint16_t *off;
+    const int32_t *tmin, *tmax;
+    int Es;
+};
+
+__host__ __device__ constexpr int64_t table_off_bytes(int64_t Es, int GS) {
+    return ((Es * GS * 2) + 15) & ~(int64_t)15;
+}
+__host__ __device__ constexpr int64_t table_bytes(int64_t Es, int GS) {
+    return table_off_bytes(Es, GS) + 8 * Es;
+}
+
+__device__ __forceinline__ fold_table table_view(const unsigned char *raw, int Es, int GS) {
+    fold_table t;
+    t.off = reinterpret_cast<const uint16_t *>(raw);
+    t.tmin = reinterpret_cast<const int32_t *>(raw + table_off_bytes(Es, GS));
+    t.tmax = t.tmin + Es;
+    t.Es = Es;
+    return t;
+}
+
+// The byte offsets of one epoch's GS periods, two per 32-bit word.
+template <int GS>
+struct packed_offsets {
+    static constexpr int W = (GS + 1) / 2;
+    uint32_t w[W];
+    __device__ __forceinline__ void load(const uint16_t *row) {
+        const uint32_t a = smem_u32(row);
+        if constexpr (GS == 8) {
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                         : "r"(a));
+        } else if constexpr (GS == 4) {
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a));
+        } else if constexpr (GS == 2) {
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w[0]) : "r"(a));
+        } else {
+            uint16_t h;
+            asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(a));
+            w[0] = h;
+        }
+    }
+    __device__ __forceinline__ uint32_t operator[](int g) const {
+        return (g & 1) ? (w[g >> 1] >> 16) : (w[g >> 1] & 0xFFFFu);
+    }
+};
+
+// Bit gg set when period g0 + gg is folded at duration D: it has epochs, D < P (Sec. 2.3)
+// and the caller's mask allows the pair (mask rows mask_k0 + g).
+template <int GS>
+__device__ __forceinline__ unsigned period_use(const fold_smem &sm, int g0, double D, int j, int J,
+                                               const uint8_t *__restrict__ mask, int mask_k0) {
+    unsigned use = 0u;
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        const int g = g0 + gg;
+        if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(mask_k0 + g) * J + j]))
+            use |= 1u << gg;
+    }
+    return use;
+}
+
+// Bounded wait of the fold, called by whole warps; the result is the same for every lane
+// (false if any lane's wait gave up, or if the phase is not complete and the block has
+// aborted). A wait that gives up records the time-out and aborts the block; the finalize
+// kernel then writes NaN for every period.
+__device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t parity,
+                                          int *status) {
+    bool ok = mbar_try(bar, parity);
+    if (!ok && !*(volatile int *)&sm.abort) {
+        ok = mbar_wait(bar, parity);
+        if (!ok) {
+            *(volatile int *)&sm.abort = 1;
+            atomicExch(status, CETRA_ETIMEOUT);
+        }
+    }
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+// Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
+// slot's best key in shared memory.
+template <int GS>
+__device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float *best_lr2,
+                                             const uint32_t *best_at) {
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        unsigned long long key =
+            best_lr2[gg] >= 0.0f ? make_key(0.5f * best_lr2[gg], best_at[gg]) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+            key = u > key ? u : key;
+        }
+        if ((threadIdx.x & 31) == 0 && key) atomicMax(&sm.best[g0 + gg], key);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Main path: tiles of T = FT_THREADS R phases, one strip per epoch.
+
+// Live epochs of a tile starting at phase i0: e < Es with tmin[e] < I - i0 (tmin is
+// nondecreasing in e, so they are a prefix); nE only shrinks as i0 grows.
+__device__ __forceinline__ int live_epochs(const fold_table &tb, int nE, int I, int i0) {
+    while (nE > 0 && tb.tmin[nE - 1] >= I - i0) --nE;
+    return nE;
+}
+
+template <int GS, int R>
+__device__ void produce_main(fold_smem &sm, float2 *strips, const fold_table &tb, int g0,
+                             int nph_sub, const float2 *__restrict__ ab, int I, int64_t ld, int J,
+                             int jlo, int jhi, const double *__restrict__ durations,
+                             const uint8_t *__restrict__ mask, int mask_k0, ring &iss,
+                             int *__restrict__ status) {
+    constexpr int T = FT_THREADS * R;
+    const bool leader = (threadIdx.x & 31) == 0;
+    for (int j = jlo; j < jhi; ++j) {
+        if (!period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0)) continue;
+        const float2 *row = ab + (int64_t)j * ld;
+        int nE = tb.Es;
+        for (int i0 = 0; i0 < nph_sub; i0 += T) {
+            nE = live_epochs(tb, nE, I, i0);
+            for (int e = 0; e < nE; ++e) {
+                if (!fold_wait(sm, &sm.empty[iss.stage], iss.parity ^ 1u, status)) return;
+                if (leader) {
+                    const int a = i0 + (tb.tmin[e] & ~1);
+                    const int len = ((i0 + tb.tmax[e] + T - a) + 1) & ~1;
+                    const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
+                    fence_proxy_async();
+                    mbar_expect_tx(&sm.full[iss.stage], bytes);
+                    bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.full[iss.stage]);
+                }
+                __syncwarp();
+                iss.next();
+            }
+        }
+    }
+}
+
+template <int GS, int R, bool KAHAN>
+__device__ void consume_main(fold_smem &sm, const float2 *strips, const fold_table &tb, int g0,
+                             int nph_sub, int I, int J, int jlo, int jhi,
+                             const double *__restrict__ durations,
+                             const uint8_t *__restrict__ mask, int mask_k0, ring &con,
+                             int *__restrict__ status) {
+    constexpr int T = FT_THREADS * R;
+    constexpr uint32_t kStageBytes = FT_STRIP * (uint32_t)sizeof(float2);
+    constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
+    const int c = threadIdx.x;
+    const uint32_t mine = smem_u32(strips) + (uint32_t)c * (uint32_t)sizeof(float2);
+    float best_lr2[GS];
+    uint32_t best_at[GS];
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        best_lr2[gg] = -1.0f;
+        best_at[gg] = 0u;
+    }
+    for (int j = jlo; j < jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+        if (!use) continue;
+        const bool all_used = use == (1u << GS) - 1u;
+        int nmin = I;  // phases every used period has
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg)
+            if ((use >> gg) & 1u) nmin = min(nmin, sm.nph[g0 + gg]);
+        int nE = tb.Es;
+        for (int i0 = 0; i0 < nph_sub; i0 += T) {
+            nE = live_epochs(tb, nE, I, i0);
+            float2 acc[GS][R];
+            float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
+            // epoch 0: every period's cell is its phase cell. (A wait that gave up ends the
+            // path at once: the main path has no block barrier, so every thread still meets the
+            // caller's next one.)
+            if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) return;
+            {
+                const uint32_t a = mine + con.stage * kStageBytes;
+                float2 v[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = lds2(a + r * kRowStep);
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[gg][r] = v[r];
+                if constexpr (KAHAN) {
+#pragma unroll
+                    for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                        for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+                }
+                mbar_arrive(&sm.empty[con.stage]);
+            }
+            con.next();
+            for (int e = 1; e < nE; ++e) {
+                if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) return;
+                const uint32_t a = mine + con.stage * kStageBytes;
+                packed_offsets<GS> off;
+                off.load(tb.off + e * GS);
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg) {
+                    if (!all_used && !((use >> gg) & 1u)) continue;
+                    const uint32_t ag = a + off[gg];
+                    float2 v[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = lds2(ag + r * kRowStep);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if constexpr (KAHAN)
+                            kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
+                        else
+                            add2(acc[gg][r], v[r]);
+                    }
+                }
+                mbar_arrive(&sm.empty[con.stage]);
+                con.next();
+            }
+            // 2 LR = SA^2 / SB per (period, phase); a null sum gives NaN, never a maximum;
+            // the running maximum keeps the first (smallest j, then smallest i) of equal values
+            const bool whole = i0 + T <= nmin;
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg) {
+                if (!((use >> gg) & 1u)) continue;
+                const int nph = sm.nph[g0 + gg];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = i0 + c + r * FT_THREADS;
+                    float2 v = acc[gg][r];
+                    if constexpr (KAHAN) add2(v, cmp[gg][r]);
+                    if (!whole && i >= nph) continue;
+                    if ((v.x * kCandidate) * v.x > best_lr2[gg] * v.y) {
+                        const float lr2 = v.x * __fdividef(v.x, v.y);
+                        if (lr2 > best_lr2[gg]) {
+                            best_lr2[gg] = lr2;
+                            best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)i;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    publish_best<GS>(sm, g0, best_lr2, best_at);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Epoch-sliced path: a sub-group whose periods all have few phases (nph <= Tp <= T/2,
+// Tp = max(32, nph)). The lanes L = c + FT_THREADS r form H = floor(T / Tp) slices of Tp
+// phases (lane L: slice L / Tp, phase L % Tp; lanes past H Tp idle); slice h folds epochs
+// e = s H + h of super-epoch s, one strip per super-epoch. The H partial sums of a phase are
+// then added in slice order through shared memory. (Strip bound: tmin grows by at most Tp
+// per epoch, since o_{e+1} - o_e <= ceil(Ps) <= Tp for the period that attains tmin[e], so a
+// super-epoch needs at most H Tp + spread + 2 <= T + spread + 2 cells; the table check keeps
+// spread <= FT_STRIP - T - 8 for this path.)
+
+__device__ __forceinline__ bool live_epoch(const fold_table &tb, int e, int I) {
+    return e < tb.Es && tb.tmin[e] < I;
+}
+
+template <int GS, int R>
+__device__ void produce_sliced(fold_smem &sm, float2 *strips, const fold_table &tb, int g0,
+                               int Tp, const float2 *__restrict__ ab, int I, int64_t ld, int J,
+                               int jlo, int jhi, const double *__restrict__ durations,
+                               const uint8_t *__restrict__ mask, int mask_k0, ring &iss,
+                               int *__restrict__ status) {
+    constexpr int T = FT_THREADS * R;
+    const int H = T / Tp;
+    const bool leader = (threadIdx.x & 31) == 0;
+    for (int j = jlo; j < jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+        if (!use) continue;
+        const float2 *row = ab + (int64_t)j * ld;
+        for (int s = 0; live_epoch(tb, s * H, I); ++s) {
+            const bool ok = fold_wait(sm, &sm.empty[iss.stage], iss.parity ^ 1u, status);
+            if (leader && ok) {
+                const int e0 = s * H;
+                const int a = tb.tmin[e0] & ~1;
+                int end = 0;
+                for (int h = 0; h < H; ++h)
+                    if (live_epoch(tb, e0 + h, I)) end = max(end, tb.tmax[e0 + h] + Tp);
+                const int len = ((end - a) + 1) & ~1;
+                const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
+                fence_proxy_async();
+                mbar_expect_tx(&sm.full[iss.stage], bytes);
+                bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.full[iss.stage]);
+            }
+            __syncwarp();
+            iss.next();
+        }
+        // the consumers' slice reduction: two block barriers per folded period
+        for (int gg = 0; gg < GS; ++gg)
+            if ((use >> gg) & 1u) {
+                block_sync();
+                block_sync();
+            }
+    }
+}
+
+template <int GS, int R, bool KAHAN>
+__device__ void consume_sliced(fold_smem &sm, const float2 *strips, float2 *part,
+                               const fold_table &tb, int g0, int Tp, int I, int J, int jlo,
+                               int jhi, const double *__restrict__ durations,
+                               const uint8_t *__restrict__ mask, int mask_k0, ring &con,
+                               int *__restrict__ status) {
+    constexpr int T = FT_THREADS * R;
+    constexpr uint32_t kStageBytes = FT_STRIP * (uint32_t)sizeof(float2);
+    const int H = T / Tp;
+    const int c = threadIdx.x;
+    const uint32_t base0 = smem_u32(strips);
+    int slice[R], phase[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int L = c + r * FT_THREADS;
+        slice[r] = L / Tp;
+        phase[r] = L - slice[r] * Tp;
+    }
+    float best_lr2[GS];
+    uint32_t best_at[GS];
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        best_lr2[gg] = -1.0f;
+        best_at[gg] = 0u;
+    }
+    for (int j = jlo; j < jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+        if (!use) continue;
+        const bool all_used = use == (1u << GS) - 1u;
+        float2 acc[GS][R];
+        float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+        if constexpr (KAHAN) {
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+        }
+        for (int s = 0; live_epoch(tb, s * H, I); ++s) {
+            if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) {
+                con.next();
+                continue;
+            }
+            const int a_s = tb.tmin[s * H] & ~1;
+            const uint32_t stage = base0 + con.stage * kStageBytes;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (slice[r] >= H) continue;  // lane past the last whole slice
+                const int e = s * H + slice[r];
+                if (!live_epoch(tb, e, I)) continue;
+                const uint32_t lb =
+                    stage + (uint32_t)(phase[r] + (tb.tmin[e] & ~1) - a_s) * (uint32_t)sizeof(float2);
+                packed_offsets<GS> off;
+                off.load(tb.off + e * GS);
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg) {
+                    if (!all_used && !((use >> gg) & 1u)) continue;
+                    const float2 v = lds2(lb + off[gg]);
+                    if constexpr (KAHAN)
+                        kahan_add2(acc[gg][r], cmp[gg][r], v);
+                    else
+                        add2(acc[gg][r], v);
+                }
+            }
+            mbar_arrive(&sm.empty[con.stage]);
+            con.next();
+        }
+        // the slices' partial sums of each phase, added in slice order
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            if (!((use >> gg) & 1u)) continue;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v = acc[gg][r];
+                if constexpr (KAHAN) add2(v, cmp[gg][r]);
+                part[c + r * FT_THREADS] = v;
+            }
+            block_sync();
+            const int nph = sm.nph[g0 + gg];
+            for (int phi = c; phi < Tp; phi += FT_THREADS) {
+                float2 v = part[phi];
+                for (int h = 1; h < H; ++h) add2(v, part[h * Tp + phi]);
+                const float lr2 = v.x * __fdividef(v.x, v.y);
+                if (phi < nph && v.y > 0.0f && lr2 > best_lr2[gg]) {
+                    best_lr2[gg] = lr2;
+                    best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)phi;
+                }
+            }
+            block_sync();
+        }
+    }
+    publish_best<GS>(sm, g0, best_lr2, best_at);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One period whose epoch table does not fit: straight from global memory (consumers only).
+__device__ void fold_direct(fold_smem &sm, int g, int mask_row, const float2 *__restrict__ ab,
+                            int I, int64_t ld, int J, int jlo, int jhi,
+                            const double *__restrict__ durations,
+                            const uint8_t *__restrict__ mask) {
+    const int c = threadIdx.x;
+    const double Ps = sm.Ps[g];
+    unsigned long long best = 0ull;
+    for (int j = jlo; j < jhi; ++j) {
+        if (!(durations[j] < sm.P[g])) continue;
+        if (mask && !mask[(int64_t)mask_row * J + j]) continue;
+        const float2 *row = ab + (int64_t)j * ld;
+        for (int i = c; i < sm.nph[g]; i += FT_THREADS) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int64_t e = 0;; ++e) {
+                const int64_t cell = i + epoch_offset(e, Ps);
+                if (cell >= I) break;
+                add2(acc, row[cell]);
+            }
+            if (acc.y > 0.0f) {
+                const float lr = 0.5f * (acc.x * __fdividef(acc.x, acc.y));
+                const unsigned long long key = make_key(lr, (uint32_t)j * (uint32_t)I + (uint32_t)i);
+                if (key > best) best = key;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = u > best ? u : best;
+    }
+    if ((c & 31) == 0 && best) atomicMax(&sm.best[g], best);
+}
+
+// ---------------------------------------------------------------------------------------------
+
+// Slot t of a group (thread t < FT_G): P, Ps = P/s in t0 steps, the number of phases and an
+// upper bound on the epochs with o_e < I.
+__device__ __forceinline__ void fold_slot_meta(fold_smem &sm, int t, bool present, double P,
+                                               int I, double c, int64_t p, int64_t q) {
+    double Ps = 0.0;
+    int nph = 0, E = 0;
+    if (present) {
+        Ps = period_steps(P, c, p, q);
+        // a period shorter than one t0 step (or not finite) has no distinct phase: null
+        if (Ps >= 1.0 && isfinite(Ps)) {
+            const double cph = ceil(Ps);
+            nph = cph < (double)I ? (int)cph : I;
+            const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
+            E = eb < 2147483647.0 ? (int)eb : 2147483647;
+        }
+    } else {
+        P = 0.0;
+    }
+    sm.P[t] = P;
+    sm.Ps[t] = Ps;
+    sm.nph[t] = nph;
+    sm.E[t] = E;
+    sm.best[t] = 0ull;
+}
+
+// Build the epoch table of sub-group [g0, g0 + GS) (all threads). Sets sm.bad when some
+// epoch's spread leaves no room for a tile in a strip, sm.tight when it leaves less than the
+// sliced path's margin. Offsets beyond the t0 grid are kept (their cells are the zero padding
+// after each grid row), so a strip never needs clipping.
+template <int GS>
+__device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, int T) {
+    uint16_t *off = reinterpret_cast<uint16_t *>(raw);
+    int32_t *tmin = reinterpret_cast<int32_t *>(raw + table_off_bytes(Es, GS));
+    int32_t *tmax = tmin + Es;
+    bool bad = false, tight = false;
+    for (int e = threadIdx.x; e < Es; e += blockDim.x) {
+        int64_t o[GS];
+        int64_t mn = INT64_MAX, mx = INT64_MIN;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            const int g = g0 + gg;
+            o[gg] = -1;
+            if (sm.E[g] > 0) {
+                int64_t v = epoch_offset(e, sm.Ps[g]);
+                v = v < (int64_t)1 << 30 ? v : (int64_t)1 << 30;
+                o[gg] = v;
+                mn = v < mn ? v : mn;
+                mx = v > mx ? v : mx;
+            }
+        }
+        const int64_t base = mn & ~(int64_t)1;
+        const int64_t spread = mx - mn;
+        if (spread > FT_STRIP - T - 2) bad = true;
+        if (spread > FT_STRIP - T - 8) tight = true;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            const int64_t d = o[gg] >= 0 ? (o[gg] - base) * (int64_t)sizeof(float2) : 0;
+            off[e * GS + gg] = (uint16_t)(d >= 0 && d < 65536 ? d : 0);
+        }
+        tmin[e] = (int32_t)mn;
+        tmax[e] = (int32_t)mx;
+    }
+    if (bad) sm.bad = 1;
+    if (tight) sm.tight = 1;
+}
+
+template <int GS, int R, bool KAHAN>
+__device__ void fold_subgroup(fold_smem &sm, float2 *strips, const fold_table &tb, float2 *part,
+                              bool sliced, int Tp, int g0, int nph_sub,
+                              const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
+                              int jhi, const double *__restrict__ durations,
+                              const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
+                              int *__restrict__ status) {
+    const bool producer = threadIdx.x >= FT_THREADS;
+    if (sliced) {
+        if (producer)
+            produce_sliced<GS, R>(sm, strips, tb, g0, Tp, ab, I, ld, J, jlo, jhi, durations, mask,
+                                  mask_k0, rg, status);
+        else
+            consume_sliced<GS, R, KAHAN>(sm, strips, part, tb, g0, Tp, I, J, jlo, jhi, durations,
+                                         mask, mask_k0, rg, status);
+    } else if (producer) {
+        produce_main<GS, R>(sm, strips, tb, g0, nph_sub, ab, I, ld, J, jlo, jhi, durations, mask,
+                            mask_k0, rg, status);
+    } else {
+        consume_main<GS, R, KAHAN>(sm, strips, tb, g0, nph_sub, I, J, jlo, jhi, durations, mask,
+                                   mask_k0, rg, status);
+    }
+}
+
+// Fold the group whose slot metadata is in `sm` over durations [jlo, jhi) of one (A, B)
+// grid: every sub-group (8 -> 4 -> 2 -> 1 periods, as the table allows) in turn; slot g's
+// best key ends in sm.best[g]. Mask rows are (mask_k0 + g). A wait that gave up leaves
+// sm.abort set.
+template <bool KAHAN, int R>
+__device__ void fold_group(fold_smem &sm, float2 *strips, unsigned char *tab, float2 *part,
+                           const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
+                           int jhi, const double *__restrict__ durations,
+                           const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
+                           int *__restrict__ status) {
+    constexpr int T = FT_THREADS * R;
+    for (int g0 = 0; g0 < FT_G;) {
+        int GS = FT_G;
+        while (g0 % GS) GS >>= 1;
+        int Es = 0;
+        bool table_ok = false;
+        for (;;) {
+            Es = 0;
+            for (int g = g0; g < g0 + GS; ++g) Es = max(Es, sm.E[g]);
+            if (Es == 0) break;  // no period of the sub-group has a phase
+            if (table_bytes(Es, GS) > FT_TAB_BYTES) {
+                if (GS > 1) {
+                    GS >>= 1;
+                    continue;
+                }
+                break;  // a single period with too many epochs: no table
+            }
+            block_sync();  // everyone is done with the previous table
+            if (threadIdx.x == 0) sm.bad = sm.tight = 0;
+            block_sync();
+            if (GS == 8)
+                build_table<8>(sm, tab, g0, Es, T);
+            else if (GS == 4)
+                build_table<4>(sm, tab, g0, Es, T);
+            else if (GS == 2)
+                build_table<2>(sm, tab, g0, Es, T);
+            else
+                build_table<1>(sm, tab, g0, Es, T);
+            block_sync();
+            if (sm.bad && GS > 1) {
+                GS >>= 1;
+                continue;
+            }
+            table_ok = !sm.bad;
+            break;
+        }
+        int nph_sub = 0;
+        for (int g = g0; g < g0 + GS; ++g) nph_sub = max(nph_sub, sm.nph[g]);
+        if (Es == 0 || nph_sub == 0) {
+            g0 += GS;
+            continue;
+        }
+        if (!table_ok) {
+            // GS == 1 here
+            if (threadIdx.x < FT_THREADS)
+                fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, jlo, jhi, durations, mask);
+            g0 += GS;
+            continue;
+        }
+        const fold_table tb = table_view(tab, Es, GS);
+        const int Tp = max(32, nph_sub);  // phases per epoch slice
+        const bool sliced = !sm.tight && 2 * Tp <= T;
+        if (GS == 8)
+            fold_subgroup<8, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+        else if (GS == 4)
+            fold_subgroup<4, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+        else if (GS == 2)
+            fold_subgroup<2, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+        else
+            fold_subgroup<1, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+        g0 += GS;
+    }
+}
+
+// Block start: barriers (the full ones expect the producer's one arrival, the empty ones one
+// arrival per consumer thread).
+__device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < FT_NSTAGE; ++st) {
+            mbar_init(&sm.full[st], 1);
+            mbar_init(&sm.empty[st], FT_THREADS);
+        }
+        fence_mbar_init();
+        sm.abort = 0;
+    }
+}
+
+// A block that aborted: the producer waits (bounded) for the copies it may still have in
+// flight, the last FT_NSTAGE it issued, so that none lands in shared memory after the block
+// exits.
+__device__ void drain_copies(fold_smem &sm, const ring &rg) {
+    if (threadIdx.x < FT_THREADS) return;
+    const uint32_t first = rg.n > FT_NSTAGE ? rg.n - FT_NSTAGE : 0u;
+    for (uint32_t n = first; n < rg.n; ++n)
+        mbar_wait(&sm.full[n % FT_NSTAGE], (n / FT_NSTAGE) & 1u);
+}
+
+__device__ __forceinline__ void fold_smem_views(unsigned char *raw, float2 *&strips,
+                                                unsigned char *&tab, float2 *&part) {
+    strips = reinterpret_cast<float2 *>(raw);
+    tab = raw + (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2);
+    part = reinterpret_cast<float2 *>(tab + FT_TAB_BYTES);
+}
+
+// Single light curve. Work item = (duration chunk, group); chunks outermost so that the blocks
+// running at the same time read the same grid rows; within a chunk the groups run from the
+// last (the longest periods of an ascending grid: the most phases, the most work) to the first.
+// accumulate = 1: several chunks per period, keys combined with atomicMax (zeroed before).
+template <bool KAHAN>
+__global__ void __launch_bounds__(FT_BLOCK, FT_MIN_BLOCKS)
+fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
+            const double *__restrict__ durations, const double *__restrict__ periods, int K,
+            const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q, int n_groups,
+            int jchunk, int accumulate, unsigned long long *__restrict__ keys,
+            int *__restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ fold_smem sm;
+    float2 *strips, *part;
+    unsigned char *tab;
+    fold_smem_views(smem_raw, strips, tab, part);
+    const int t = threadIdx.x;
+    const int jc = blockIdx.x / n_groups;
+    const int grp = n_groups - 1 - (int)(blockIdx.x % n_groups);
+    const int jlo = jc * jchunk, jhi = min(J, jlo + jchunk);
+    const int k0 = grp * FT_G;
+    fold_init_barriers(sm);
+    if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
+    block_sync();
+    ring rg;
+    constexpr int R = KAHAN ? FT_R / 2 : FT_R;
+    fold_group<KAHAN, R>(sm, strips, tab, part, ab, I, ld, J, jlo, jhi, durations, mask, k0, rg,
+                         status);
+    block_sync();
+    if (sm.abort) {
+        drain_copies(sm, rg);
+        return;
+    }
+    if (t < FT_G && k0 + t < K) {
+        const unsigned long long v = sm.best[t];
+        if (!accumulate)
+            keys[k0 + t] = v;
+        else if (v)
+            atomicMax(&keys[k0 + t], v);
+    }
+}
+
+// Batched form: persistent blocks drain a queue of (curve, group of FT_G periods) items; each
+// group's best per period goes into the curve's key (LR bits, inverted period index: the
+// largest LR wins, ties to the smallest period index).
+template <bool KAHAN, int R>
+__global__ void __launch_bounds__(FT_BLOCK, FT_MIN_BLOCKS)
+batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
+                  const int64_t *__restrict__ group_off, int n_curves, int64_t n_items, int J,
+                  const double *__restrict__ durations, double c, int64_t p, int64_t q,
+                  int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
+                  unsigned long long *__restrict__ curve_keys, int *__restrict__ status,
+                  const int64_t *__restrict__ item_list,
+                  const unsigned long long *__restrict__ n_items_dev) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ fold_smem sm;
+    __shared__ int s_item;
+    // the queue length: n_items, or the count a device-side selection left (capped by n_items)
+    if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
+    float2 *strips, *part;
+    unsigned char *tab;
+    fold_smem_views(smem_raw, strips, tab, part);
+    const int t = threadIdx.x;
+    fold_init_barriers(sm);
+    ring rg;
+    for (;;) {
+        block_sync();  // the previous item is done with the shared state
+        if (t == 0) s_item = atomicAdd(queue, 1);
+        block_sync();
+        if (s_item >= n_items) break;
+        // queue position -> work item: the position itself, or the caller's list entry
+        const int64_t item = item_list ? item_list[s_item] : (int64_t)s_item;
+        const int cidx = csr_find(group_off, n_curves, item);
+        const batch_curve cv = curves[cidx];
+        const int k0 = (int)(item - group_off[cidx]) * FT_G;
+        if (t < FT_G) {
+            const bool present = k0 + t < cv.n_periods;
+            fold_slot_meta(sm, t, present, present ? batch_period(cv.pmin, cv.ratio, k0 + t) : 0.0,
+                           cv.I, c, p, q);
+        }
+        block_sync();
+        fold_group<KAHAN, R>(sm, strips, tab, part, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
+                             durations, nullptr, 0, rg, status);
+        block_sync();
+        if (sm.abort) {
+            drain_copies(sm, rg);
+            return;
+        }
+        if (t < FT_G && k0 + t < cv.n_periods) {
+            const unsigned long long v = sm.best[t];
+            period_keys[cv.per_off + k0 + t] = v;
+            if (v != 0ull)
+                atomicMax(&curve_keys[cidx], (v & 0xFFFFFFFF00000000ull) |
+                                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)(k0 + t)));
+        }
+    }
+}
+
+}  // namespace
+
+size_t fold_smem_bytes() {
+    return (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2) + (size_t)FT_TAB_BYTES +
+           (size_t)FT_T * sizeof(float2);
+}
+
+cudaError_t fold_configure() {
+    const int bytes = (int)fold_smem_bytes();
+    for (auto fn : {fold_kernel<false>, fold_kernel<true>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    for (auto fn : {batch_fold_kernel<false, FT_R>, batch_fold_kernel<false, FT_R / 2>,
+                    batch_fold_kernel<true, FT_R / 2>}) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
+                        const double *periods, int K, const uint8_t *mask,
+                        unsigned long long *keys, int *status) {
+    if (K <= 0) return cudaSuccess;
+    const int n_groups = (K + FT_G - 1) / FT_G;
+    const size_t grid_bytes = (size_t)plan->J * (size_t)plan->ab_ld * sizeof(float2);
+    const int jchunk = grid_bytes > FT_L2_GRID_BYTES ? 1 : plan->J;
+    const int n_chunks = (plan->J + jchunk - 1) / jchunk;
+    const int64_t items = (int64_t)n_groups * n_chunks;
+    if (items > 2147483647) return cudaErrorInvalidConfiguration;
+    const int accumulate = n_chunks > 1;
+    if (accumulate) {
+        cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)K * sizeof(unsigned long long), ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    prof_mark(ctx, KID_FOLD, true);
+    auto kern = plan->precision == CETRA_FP32_KAHAN ? fold_kernel<true> : fold_kernel<false>;
+    kern<<<(unsigned)items, FT_BLOCK, fold_smem_bytes(), ctx->stream>>>(
+        ab, (int)plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
+        plan->cadence, plan->p, plan->q, n_groups, jchunk, accumulate, keys, status);
+    prof_mark(ctx, KID_FOLD, false);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+// Fold variants the autotuner chooses from: phases per thread (FT_R or FT_R / 2).
+int batch_fold_variants() { return 2; }
+int batch_fold_blocks_per_sm(int) { return FT_MIN_BLOCKS; }
+
+cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
+                              const float2 *ab, const batch_curve *curves,
+                              const int64_t *group_off, int n_curves, int64_t n_items,
+                              int *queue, unsigned long long *period_keys,
+                              unsigned long long *curve_keys, int *status,
+                              const int64_t *item_list, const unsigned long long *n_items_dev) {
+    if (n_items <= 0) return cudaSuccess;
+    auto kern = batch_fold_kernel<false, FT_R>;
+    if (plan->precision == CETRA_FP32_KAHAN)
+        kern = batch_fold_kernel<true, FT_R / 2>;
+    else if (variant == 1)
+        kern = batch_fold_kernel<false, FT_R / 2>;
+    kern<<<blocks, FT_BLOCK, fold_smem_bytes(), stream>>>(
+        ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
+        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list, n_items_dev);
+    return cudaGetLastError();
+}

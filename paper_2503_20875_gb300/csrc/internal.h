@@ -92,11 +92,11 @@ struct cetra_linear_grid {
 // stride-RB shared-memory reads of a warp fall in distinct banks.
 constexpr int LIN_RB = 9;
 constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear kernel
-constexpr int FOLD_THREADS = 256;
-
-// Fold kernel shape (compile-time; see fold_tma_kernel).
+// Fold kernel shape (fold.cu, compile-time). A block is FT_THREADS consumer threads, each
+// folding FT_R phases of every period of a group of up to FT_G periods, plus one producer warp
+// that issues the bulk copies of the staged strips.
 #ifndef FT_R
-#define FT_R 4            // phases per thread
+#define FT_R 4            // phases per consumer thread
 #endif
 #ifndef FT_STRIP
 #define FT_STRIP 2560     // cells per staged strip
@@ -107,14 +107,25 @@ constexpr int FOLD_THREADS = 256;
 #ifndef FT_MIN_BLOCKS
 #define FT_MIN_BLOCKS 2
 #endif
-constexpr int FT_THREADS = 256;
-constexpr int FT_T = FT_THREADS * FT_R;  // phases per tile
-constexpr int FT_G = 8;                  // periods per block
-constexpr int FT_TABLE = 8192;           // epoch-offset table entries (32 KiB)
+#ifndef FT_TAB_BYTES
+#define FT_TAB_BYTES (40 * 1024)  // epoch table: u16 offsets + two int32 per epoch
+#endif
+#ifndef FT_CWARPS
+#define FT_CWARPS 7       // consumer warps per block (+ the producer warp: 8 warps, 128 registers)
+#endif
+constexpr int FT_THREADS = FT_CWARPS * 32;           // consumer threads
+constexpr int FT_BLOCK = FT_THREADS + 32;            // + the producer warp
+constexpr int FT_T = FT_THREADS * FT_R;              // phases per tile
+constexpr int FT_G = 8;                              // periods per group
 constexpr long long FT_WAIT_CYCLES = 2000000000ll;  // ~1 s of SM clocks before a wait gives up
 constexpr uint32_t FT_SUSPEND_NS = 20000;            // suspend hint of one barrier try
 constexpr int FOLD_PAD = FT_STRIP + 16;  // zero cells after each grid row
+// (A, B) grids larger than this are folded one duration per work item, so that the blocks
+// running at the same time read one row and the L2 holds it
+constexpr size_t FT_L2_GRID_BYTES = (size_t)64 << 20;
 size_t fold_smem_bytes();
+// Opt the fold kernels in to their dynamic shared memory (fold.cu).
+cudaError_t fold_configure();
 
 // Device view of one light curve of a batch (cetra_batch_*).
 struct batch_curve {

@@ -3,7 +3,7 @@
 //   resample_kernel   Sec. 2.1.1  nearest-grid-point scatter of (W y, W), W = 1/sigma^2
 //   linear_kernel     Sec. 2.2    per (duration, t0): A = sum m W y, B = sum m^2 W over the
 //                                 window; depth = A/B, var = 1/B, dlogl = A^2/(2B)
-//   fold_tma_kernel   Sec. 2.3    per group of periods: sum A and B over the epoch cells of
+//   (fold.cu)         Sec. 2.3    per group of periods: sum A and B over the epoch cells of
 //                                 every (duration, phase), LR = SA^2/(2 SB), in-kernel max/argmax
 //   finalize_kernel   Sec. 2.3    FP64 re-sum of each period's winner: Z, var_Z, LR, t0
 //   logl0_kernel      Sec. 2.2    constant-flux log-likelihood (Eq. 1 at zero depth)
@@ -16,78 +16,11 @@
 #include <cfloat>
 #include <cstdint>
 
+#include "device.cuh"
 #include "internal.h"
 
 namespace {
 
-__device__ __forceinline__ unsigned long long pack2(float2 v) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-    return r;
-}
-
-__device__ __forceinline__ float2 unpack2(unsigned long long r) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-}
-
-// acc += a * b elementwise with one packed FP32x2 fused multiply-add.
-__device__ __forceinline__ void fma2(float2 &acc, float2 a, float2 b) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(acc)));
-    acc = unpack2(d);
-}
-
-// acc += v elementwise with one packed FP32x2 add.
-__device__ __forceinline__ void add2(float2 &acc, float2 v) {
-#ifdef CETRA_SCALAR_ADD
-    acc.x += v.x;
-    acc.y += v.y;
-#else
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(acc)), "l"(pack2(v)));
-    acc = unpack2(d);
-#endif
-}
-
-// d = a - b elementwise with one packed FP32x2 subtract.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
-    return unpack2(d);
-}
-
-// Kahan-compensated s += a * b on (A, B) pairs; nc carries minus the running
-// compensation: y = a b + nc, t = s + y, nc = y - (t - s), s = t.
-__device__ __forceinline__ void kahan_fma2(float2 &s, float2 &nc, float2 a, float2 b) {
-    float2 y = nc;
-    fma2(y, a, b);
-    float2 t = s;
-    add2(t, y);
-    nc = sub2(y, sub2(t, s));
-    s = t;
-}
-
-// Kahan-compensated s += v on (A, B) pairs (nc as above).
-__device__ __forceinline__ void kahan_add2(float2 &s, float2 &nc, float2 v) {
-    float2 y = v;
-    add2(y, nc);
-    float2 t = s;
-    add2(t, y);
-    nc = sub2(y, sub2(t, s));
-    s = t;
-}
-
-// Nearest epoch cell offset o_e = floor(e Ps + 1/2), FP64, no contraction.
-__device__ __forceinline__ int64_t epoch_offset(int64_t e, double Ps) {
-    return (int64_t)floor(__dadd_rn(__dmul_rn((double)e, Ps), 0.5));
-}
-
-// Period in t0 steps, Ps = (P q) / (c p), FP64, no contraction.
-__device__ __forceinline__ double period_steps(double P, double c, int64_t p, int64_t q) {
-    return __ddiv_rn(__dmul_rn(P, (double)q), __dmul_rn(c, (double)p));
-}
 
 // --------------------------------------------------------------------------------------------
 // Sec. 2.1.1: each observation goes to the nearest grid point
@@ -262,647 +195,6 @@ linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t
                                    dlogl);
 }
 
-// Per-period key: larger LR wins; on equal LR the smaller flat index j*I + i wins
-// (smallest duration, then smallest t0). LR >= 0, so its float bits order like uint.
-__device__ __forceinline__ unsigned long long make_key(float lr, uint32_t flat) {
-    return ((unsigned long long)__float_as_uint(lr) << 32) | (unsigned long long)(0xFFFFFFFFu - flat);
-}
-
-__device__ __forceinline__ unsigned long long block_max_key(unsigned long long v,
-                                                            unsigned long long *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long u = __shfl_down_sync(0xFFFFFFFFu, v, o);
-        v = u > v ? u : v;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        v = lane < nw ? red[lane] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long u = __shfl_down_sync(0xFFFFFFFFu, v, o);
-            v = u > v ? u : v;
-        }
-    }
-    return v;
-}
-
-// --------------------------------------------------------------------------------------------
-// Shared-memory barriers and 1-D bulk copies (TMA) used by the fold.
-__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-// global -> shared bulk copy; src and dst 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
-                                          uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-// Potentially blocking test of a barrier phase: the thread may be suspended (up
-// to the hinted time) instead of spinning, so waiting warps do not take issue slots.
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(FT_SUSPEND_NS)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false if the phase did not complete within FT_WAIT_CYCLES SM clocks.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (clock64() - t0 > FT_WAIT_CYCLES) return false;
-    }
-}
-
-// --------------------------------------------------------------------------------------------
-// Sec. 2.3 periodic search. One block folds a group of FT_G consecutive trial periods
-// over every duration. Neighbouring periods gather nearly the same epoch cells, so
-// for a tile of FT_T phases and an epoch e the block copies the union of the cells
-// the group needs, [i0 + min_g o_e(g), i0 + max_g o_e(g) + FT_T), into shared memory
-// with one bulk copy (FT_NSTAGE-deep ring, one mbarrier per stage) and every period
-// reads its cells from there: the grid is read from L2 about once per group instead
-// of once per period. Thread t owns phases i0 + t + r * FT_THREADS (r < FT_R) of
-// every period of the group, summing (A, B) over epochs in ascending order.
-// Grid rows carry FOLD_PAD zero cells after the last t0, so a strip never needs
-// clipping: cells past the end contribute (0, 0).
-// Groups whose offsets spread too far apart for one strip are split (8 -> 4 -> 2 -> 1);
-// a period with more epochs than the offset table holds is folded straight from
-// global memory with its offsets computed in FP64 on the fly.
-constexpr int32_t FT_SENT = INT32_MAX;  // epoch past the end of the t0 grid
-
-// Shared state of the fold block.
-struct fold_smem {
-    uint64_t bar[FT_NSTAGE];  // stage filled (bulk copy landed)
-    unsigned long long red[FT_THREADS / 32];
-    unsigned long long best[FT_G][FT_THREADS];
-    double P[FT_G], Ps[FT_G];
-    int nph[FT_G];
-    int E[FT_G];
-    int bad;
-    int tight;  // some epoch's spread leaves less than the sliced path's margin
-};
-
-// Ring of bulk copies: `n` counts copies issued (thread 0) or consumed (all threads);
-// copy n lands in stage n % FT_NSTAGE, completing phase n / FT_NSTAGE of that stage's `bar`.
-// The block meets at a barrier after every epoch (which also votes on wait time-outs), so
-// thread 0 may refill the stage read two epochs earlier. (Per-stage drain barriers instead,
-// with warps drifting up to two epochs apart, measured 0.6-2 % faster on the largest
-// workloads but 11-13 % slower on small ones and on the compensated path.)
-struct ring {
-    uint32_t n = 0, stage = 0, parity = 0;
-    __device__ void next() {
-        ++n;
-        if (++stage == FT_NSTAGE) {
-            stage = 0;
-            parity ^= 1u;
-        }
-    }
-};
-
-// The GS strip offsets of one epoch, with 16-byte shared loads where the row allows.
-template <int GS>
-__device__ __forceinline__ void load_offsets(const int32_t *de, int32_t *dv) {
-    if constexpr (GS % 4 == 0) {
-#pragma unroll
-        for (int v = 0; v < GS / 4; ++v) {
-            const int4 x = reinterpret_cast<const int4 *>(de)[v];
-            dv[4 * v] = x.x;
-            dv[4 * v + 1] = x.y;
-            dv[4 * v + 2] = x.z;
-            dv[4 * v + 3] = x.w;
-        }
-    } else {
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg) dv[gg] = de[gg];
-    }
-}
-
-// Fold one sub-group of GS periods [g0, g0 + GS) whose table is built: offsets relative
-// to the epoch's strip start, d[e][gg] = o_e(g) - tmin[e] (FT_SENT: no cell),
-// tmin[e], tlen[e] (strip spread) and full[e] (every period has a cell at epoch e).
-// R phases per thread (tile FT_THREADS * R <= FT_T); KAHAN: compensated epoch sums.
-// Returns false if a bulk copy timed out (the block must stop).
-template <int GS, int R, bool KAHAN>
-__device__ bool fold_subgroup(fold_smem &sm, float2 *strips, const int32_t *tab, int Es, int g0,
-                              int k0, const float2 *__restrict__ ab, int I, int64_t ld, int J,
-                              const double *__restrict__ durations,
-                              const uint8_t *__restrict__ mask, ring &iss, ring &con,
-                              int *__restrict__ status) {
-    const int t = threadIdx.x;
-    const int32_t *d = tab;
-    const int32_t *tmin = tab + Es * GS;
-    const int32_t *tlen = tmin + Es;
-    const int32_t *full = tlen + Es;
-    int nph_sub = 0;
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg) nph_sub = max(nph_sub, sm.nph[g0 + gg]);
-    float best_lr[GS];
-    uint32_t best_at[GS];
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg) {
-        best_lr[gg] = -1.0f;
-        best_at[gg] = 0u;
-    }
-    for (int j = 0; j < J && nph_sub > 0; ++j) {
-        const double D = durations[j];
-        unsigned use = 0u;
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg) {
-            const int g = g0 + gg;
-            if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(k0 + g) * J + j]))
-                use |= 1u << gg;
-        }
-        if (!use) continue;
-        const bool all_used = use == (1u << GS) - 1u;
-        const float2 *row = ab + (int64_t)j * ld;
-        constexpr int T = FT_THREADS * R;
-        for (int i0 = 0; i0 < nph_sub; i0 += T) {
-            float2 acc[GS][R];
-            float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
-#pragma unroll
-            for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
-            if constexpr (KAHAN) {
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                    for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
-            }
-            // (tmin[e] is FT_SENT when no period reaches epoch e: compare without adding)
-            auto live = [&](int e) { return e < Es && tmin[e] < I - i0; };
-            auto issue = [&](int e) {
-                const int a = (i0 + tmin[e]) & ~1;
-                const int len = ((i0 + tmin[e] + tlen[e] + T - a) + 1) & ~1;
-                const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
-                fence_proxy_async();
-                mbar_expect_tx(&sm.bar[iss.stage], bytes);
-                bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
-                iss.next();
-            };
-            if (t == 0)
-                for (int e = 0; e < FT_NSTAGE - 1 && live(e); ++e) issue(e);
-            for (int e = 0; live(e); ++e) {
-                if (t == 0 && live(e + FT_NSTAGE - 1)) issue(e + FT_NSTAGE - 1);
-                const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
-                const float2 *S = strips + con.stage * FT_STRIP + ((i0 + tmin[e]) & 1) + t;
-                con.next();
-                const int32_t *de = d + e * GS;
-                if (!KAHAN && all_used && full[e] && e == 0) {
-                    // every period's epoch-0 offset is 0: one load serves the whole group
-                    // (3.5 % faster on the 20-s curve; 1 % slower with compensated sums)
-                    float2 v[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = S[r * FT_THREADS];
-#pragma unroll
-                    for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                        for (int r = 0; r < R; ++r) add2(acc[gg][r], v[r]);
-                } else if (all_used && full[e]) {
-                    int32_t dv[GS];
-                    load_offsets<GS>(de, dv);
-#pragma unroll
-                    for (int gg = 0; gg < GS; ++gg) {
-                        const float2 *src = S + dv[gg];
-                        float2 v[R];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] = src[r * FT_THREADS];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if constexpr (KAHAN)
-                                kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
-                            else
-                                add2(acc[gg][r], v[r]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int gg = 0; gg < GS; ++gg) {
-                        const int32_t dg = de[gg];
-                        if (dg == FT_SENT || !((use >> gg) & 1u)) continue;
-                        const float2 *src = S + dg;
-                        float2 v[R];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] = src[r * FT_THREADS];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            if constexpr (KAHAN)
-                                kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
-                            else
-                                add2(acc[gg][r], v[r]);
-                        }
-                    }
-                }
-                if (__syncthreads_or(!ok)) {
-                    // a copy did not land in time: record it, drain the ring, stop
-                    if (t == 0) {
-                        atomicExch(status, CETRA_ETIMEOUT);
-                        while (con.n < iss.n) {
-                            mbar_wait(&sm.bar[con.stage], con.parity);
-                            con.next();
-                        }
-                    }
-                    return false;
-                }
-            }
-            // 2 LR = SA^2 / SB per (period, phase) (a null sum gives NaN, never a maximum);
-            // the running max keeps the first (smallest j, then smallest i) of equal values
-#pragma unroll
-            for (int gg = 0; gg < GS; ++gg) {
-                if (!((use >> gg) & 1u)) continue;
-                const int nph = sm.nph[g0 + gg];
-                const bool whole = i0 + T <= nph;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = i0 + t + r * FT_THREADS;
-                    float2 v = acc[gg][r];
-                    if constexpr (KAHAN) add2(v, cmp[gg][r]);
-                    const float lr2 = v.x * __fdividef(v.x, v.y);
-                    if ((whole || i < nph) && lr2 > best_lr[gg]) {
-                        best_lr[gg] = lr2;
-                        best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)i;
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg)
-        if (best_lr[gg] >= 0.0f) {
-            const unsigned long long key = make_key(0.5f * best_lr[gg], best_at[gg]);
-            if (key > sm.best[g0 + gg][t]) sm.best[g0 + gg][t] = key;
-        }
-    return true;
-}
-
-// A sub-group whose periods all have few phases (nph <= Tp <= T/2, Tp = max(32, nph)):
-// the lanes L = t + FT_THREADS r of the block form H = floor(T / Tp) epoch slices of Tp
-// phases (lane L: slice L / Tp, phase L % Tp; lanes past H Tp idle); slice h folds epochs
-// e = s H + h of super-epoch s, and one bulk copy per super-epoch covers its H epochs. The
-// H partial sums of every phase are then added in slice order through shared memory.
-// (Strip bound: tmin grows by at most Tp per epoch (o_{e+1} - o_e <= ceil(Ps) <= Tp for the
-// period that attains tmin[e]), so a super-epoch needs at most H Tp + spread + 2 <=
-// T + spread + 2 cells; the table check keeps spread <= FT_STRIP - FT_T - 8 for this path.)
-template <int GS, int R, bool KAHAN>
-__device__ bool fold_subgroup_sliced(fold_smem &sm, float2 *strips, const int32_t *tab, int Es,
-                                     int g0, int mask_k0, const float2 *__restrict__ ab, int I,
-                                     int64_t ld, int J, const double *__restrict__ durations,
-                                     const uint8_t *__restrict__ mask, ring &iss, ring &con,
-                                     int *__restrict__ status, int Tp) {
-    constexpr int T = FT_THREADS * R;
-    const int H = T / Tp;
-    int slice[R], phase[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int L = threadIdx.x + r * FT_THREADS;
-        slice[r] = L / Tp;
-        phase[r] = L - slice[r] * Tp;
-    }
-    const int t = threadIdx.x;
-    const int32_t *d = tab;
-    const int32_t *tmin = tab + Es * GS;
-    const int32_t *tlen = tmin + Es;
-    const int32_t *full = tlen + Es;
-    float best_lr[GS];
-    uint32_t best_at[GS];
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg) {
-        best_lr[gg] = -1.0f;
-        best_at[gg] = 0u;
-    }
-    auto live_epoch = [&](int e) { return e < Es && tmin[e] < I; };
-    for (int j = 0; j < J; ++j) {
-        const double D = durations[j];
-        unsigned use = 0u;
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg) {
-            const int g = g0 + gg;
-            if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(mask_k0 + g) * J + j]))
-                use |= 1u << gg;
-        }
-        if (!use) continue;
-        const bool all_used = use == (1u << GS) - 1u;
-        const float2 *row = ab + (int64_t)j * ld;
-        float2 acc[GS][R];
-        float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
-        if constexpr (KAHAN) {
-#pragma unroll
-            for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
-        }
-        auto issue = [&](int sidx) {
-            const int e0 = sidx * H;
-            const int a = tmin[e0] & ~1;
-            int end = 0;
-            for (int h = 0; h < H; ++h)
-                if (live_epoch(e0 + h)) end = max(end, tmin[e0 + h] + tlen[e0 + h] + Tp);
-            const int len = ((end - a) + 1) & ~1;
-            const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
-            fence_proxy_async();
-            mbar_expect_tx(&sm.bar[iss.stage], bytes);
-            bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.bar[iss.stage]);
-            iss.next();
-        };
-        if (t == 0)
-            for (int sidx = 0; sidx < FT_NSTAGE - 1 && live_epoch(sidx * H); ++sidx) issue(sidx);
-        for (int sidx = 0; live_epoch(sidx * H); ++sidx) {
-            if (t == 0 && live_epoch((sidx + FT_NSTAGE - 1) * H)) issue(sidx + FT_NSTAGE - 1);
-            const bool ok = mbar_wait(&sm.bar[con.stage], con.parity);
-            const float2 *S = strips + con.stage * FT_STRIP - (tmin[sidx * H] & ~1);
-            con.next();
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (slice[r] >= H) continue;  // lane past the last whole slice
-                const int e = sidx * H + slice[r];
-                if (!live_epoch(e)) continue;
-                const float2 *src = S + phase[r] + tmin[e];
-                const int32_t *de = d + e * GS;
-                const bool fast = all_used && full[e];
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg) {
-                    const int32_t dg = de[gg];
-                    if (!fast && (dg == FT_SENT || !((use >> gg) & 1u))) continue;
-                    if constexpr (KAHAN)
-                        kahan_add2(acc[gg][r], cmp[gg][r], src[dg]);
-                    else
-                        add2(acc[gg][r], src[dg]);
-                }
-            }
-            if (__syncthreads_or(!ok)) {
-                if (t == 0) {
-                    atomicExch(status, CETRA_ETIMEOUT);
-                    while (con.n < iss.n) {
-                        mbar_wait(&sm.bar[con.stage], con.parity);
-                        con.next();
-                    }
-                }
-                return false;
-            }
-        }
-        // every copy is consumed: the strip ring is free to hold one period's partial sums
-        float2 *part = strips;
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg) {
-            if (!((use >> gg) & 1u)) continue;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 v = acc[gg][r];
-                if constexpr (KAHAN) add2(v, cmp[gg][r]);
-                part[t + r * FT_THREADS] = v;
-            }
-            __syncthreads();
-            const int nph = sm.nph[g0 + gg];
-            for (int phi = t; phi < Tp; phi += FT_THREADS) {
-                float2 v = part[phi];
-                for (int h = 1; h < H; ++h) add2(v, part[h * Tp + phi]);
-                const float lr = 0.5f * (v.x * __fdividef(v.x, v.y));
-                if (phi < nph && v.y > 0.0f && lr > best_lr[gg]) {
-                    best_lr[gg] = lr;
-                    best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)phi;
-                }
-            }
-            __syncthreads();
-        }
-    }
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg)
-        if (best_lr[gg] >= 0.0f) {
-            const unsigned long long key = make_key(best_lr[gg], best_at[gg]);
-            if (key > sm.best[g0 + gg][t]) sm.best[g0 + gg][t] = key;
-        }
-    return true;
-}
-
-// One period whose offsets do not fit the table: straight from global memory.
-__device__ void fold_direct(fold_smem &sm, int g, int k, const float2 *__restrict__ ab, int I,
-                            int64_t ld, int J, const double *__restrict__ durations,
-                            const uint8_t *__restrict__ mask) {
-    const int t = threadIdx.x;
-    const double Ps = sm.Ps[g];
-    for (int j = 0; j < J; ++j) {
-        if (!(durations[j] < sm.P[g])) continue;
-        if (mask && !mask[(int64_t)k * J + j]) continue;
-        const float2 *row = ab + (int64_t)j * ld;
-        for (int i = t; i < sm.nph[g]; i += blockDim.x) {
-            float2 acc = make_float2(0.f, 0.f);
-            for (int64_t e = 0;; ++e) {
-                const int64_t cell = i + epoch_offset(e, Ps);
-                if (cell >= I) break;
-                add2(acc, row[cell]);
-            }
-            if (acc.y > 0.0f) {
-                const float lr = 0.5f * (acc.x * __fdividef(acc.x, acc.y));
-                const unsigned long long key = make_key(lr, (uint32_t)j * (uint32_t)I + (uint32_t)i);
-                if (key > sm.best[g][t]) sm.best[g][t] = key;
-            }
-        }
-    }
-}
-
-// Per-period metadata of slot t of a group (thread t < FT_G): P, Ps = P/s in t0 steps,
-// the number of phases and an upper bound on the epochs with o_e < I.
-__device__ __forceinline__ void fold_slot_meta(fold_smem &sm, int t, bool present, double P,
-                                               int I, double c, int64_t p, int64_t q) {
-    double Ps = 0.0;
-    int nph = 0, E = 0;
-    if (present) {
-        Ps = period_steps(P, c, p, q);
-        // a period shorter than one t0 step (or not finite) has no distinct phase: null
-        if (Ps >= 1.0 && isfinite(Ps)) {
-            const double cph = ceil(Ps);
-            nph = cph < (double)I ? (int)cph : I;
-            const double eb = floor(__ddiv_rn((double)I + 0.5, Ps)) + 1.0;
-            E = eb < 2147483647.0 ? (int)eb : 2147483647;
-        }
-    } else {
-        P = 0.0;
-    }
-    sm.P[t] = P;
-    sm.Ps[t] = Ps;
-    sm.nph[t] = nph;
-    sm.E[t] = E;
-}
-
-// Fold the group whose slot metadata is in `sm` over one (A, B) grid: every sub-group
-// (8 -> 4 -> 2 -> 1 periods, as their offsets allow) in turn; the per-thread best key
-// of slot g ends in sm.best[g][t]. mask rows are (mask_k0 + g). Returns false if a
-// bulk copy timed out (uniform across the block).
-template <bool KAHAN, int R>
-__device__ bool fold_group(fold_smem &sm, float2 *strips, int32_t *tab,
-                           const float2 *__restrict__ ab, int I, int64_t ld, int J,
-                           const double *__restrict__ durations, const uint8_t *__restrict__ mask,
-                           int mask_k0, ring &iss, ring &con, int *__restrict__ status) {
-    const int t = threadIdx.x;
-    for (int g = 0; g < FT_G; ++g) sm.best[g][t] = 0ull;
-    __syncthreads();
-    for (int g0 = 0; g0 < FT_G;) {
-        // choose the sub-group [g0, g0 + Gs) and build its table:
-        // d [Es][Gs], tmin [Es], tlen [Es], full [Es]
-        int Gs = FT_G;
-        while (g0 % Gs) Gs >>= 1;
-        int Es = 0;
-        bool table_ok = false;
-        for (;;) {
-            Es = 0;
-            for (int g = g0; g < g0 + Gs; ++g) Es = max(Es, sm.E[g]);
-            if ((int64_t)Es * (Gs + 3) > FT_TABLE) {
-                if (Gs > 1) {
-                    Gs >>= 1;
-                    continue;
-                }
-                break;  // a single period with too many epochs: no table
-            }
-            __syncthreads();
-            if (t == 0) sm.bad = sm.tight = 0;
-            int32_t *tmin = tab + Es * Gs, *tlen = tmin + Es, *full = tlen + Es;
-            bool bad = false, tight = false;
-            for (int e = t; e < Es; e += blockDim.x) {
-                int32_t o[FT_G];
-                int32_t mn = FT_SENT, mx = -1, nvalid = 0;
-                for (int gg = 0; gg < Gs; ++gg) {
-                    const int g = g0 + gg;
-                    o[gg] = FT_SENT;
-                    if (e < sm.E[g]) {
-                        const int64_t v = epoch_offset(e, sm.Ps[g]);
-                        if (v < I) o[gg] = (int32_t)v;
-                    }
-                    if (o[gg] != FT_SENT) {
-                        mn = min(mn, o[gg]);
-                        mx = max(mx, o[gg]);
-                        ++nvalid;
-                    }
-                }
-                for (int gg = 0; gg < Gs; ++gg)
-                    tab[e * Gs + gg] = o[gg] == FT_SENT ? FT_SENT : o[gg] - mn;
-                tmin[e] = mn;
-                tlen[e] = mx - mn;  // < 0 when no period reaches epoch e
-                full[e] = nvalid == Gs;
-                if (mx - mn > FT_STRIP - FT_T - 2) bad = true;
-                if (mx - mn > FT_STRIP - FT_T - 8) tight = true;
-            }
-            if (bad) sm.bad = 1;
-            if (tight) sm.tight = 1;
-            __syncthreads();
-            if (sm.bad && Gs > 1) {
-                Gs >>= 1;
-                continue;
-            }
-            table_ok = !sm.bad;
-            break;
-        }
-        // periods with few phases: fold several epochs at once (epoch slices)
-        int nph_sub = 0;
-        for (int g = g0; g < g0 + Gs; ++g) nph_sub = max(nph_sub, sm.nph[g]);
-        const int tp = max(32, nph_sub);  // phases per epoch slice
-        const bool sliced = table_ok && !sm.tight && nph_sub > 0 &&
-                            2 * tp <= FT_THREADS * R;
-        bool ok = true;
-        if (!table_ok) {
-            fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, durations, mask);
-        } else if (sliced) {
-            if (Gs == 8)
-                ok = fold_subgroup_sliced<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
-                                                       ld, J, durations, mask, iss, con, status,
-                                                       tp);
-            else if (Gs == 4)
-                ok = fold_subgroup_sliced<4, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
-                                                       ld, J, durations, mask, iss, con, status,
-                                                       tp);
-            else if (Gs == 2)
-                ok = fold_subgroup_sliced<2, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
-                                                       ld, J, durations, mask, iss, con, status,
-                                                       tp);
-            else
-                ok = fold_subgroup_sliced<1, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I,
-                                                       ld, J, durations, mask, iss, con, status,
-                                                       tp);
-        } else if (Gs == 8) {
-            ok = fold_subgroup<8, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
-                                            durations, mask, iss, con, status);
-        } else if (Gs == 4) {
-            ok = fold_subgroup<4, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
-                                            durations, mask, iss, con, status);
-        } else if (Gs == 2) {
-            ok = fold_subgroup<2, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
-                                            durations, mask, iss, con, status);
-        } else {
-            ok = fold_subgroup<1, R, KAHAN>(sm, strips, tab, Es, g0, mask_k0, ab, I, ld, J,
-                                            durations, mask, iss, con, status);
-        }
-        if (!ok) return false;
-        g0 += Gs;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < FT_NSTAGE; ++st) mbar_init(&sm.bar[st], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-}
-
-template <bool KAHAN>
-__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
-fold_tma_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
-                const double *__restrict__ durations, const double *__restrict__ periods, int K,
-                const uint8_t *__restrict__ mask, double c, int64_t p, int64_t q,
-                unsigned long long *__restrict__ keys, int *__restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2 *strips = reinterpret_cast<float2 *>(smem_raw);                      // [NSTAGE][STRIP]
-    int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);  // FT_TABLE
-    __shared__ fold_smem sm;
-    const int t = threadIdx.x;
-    fold_init_barriers(sm);
-    ring iss, con;
-    const int ngroups = (K + FT_G - 1) / FT_G;
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int k0 = grp * FT_G;
-        __syncthreads();  // the previous group is done with the shared tables
-        if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
-        if (!fold_group<KAHAN, KAHAN ? FT_R / 2 : FT_R>(sm, strips, tab, ab, I, ld, J, durations,
-                                                         mask, k0, iss, con, status))
-            return;  // uniform: every thread saw the same vote
-        for (int g = 0; g < FT_G; ++g) {
-            const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
-            if (t == 0 && k0 + g < K) keys[k0 + g] = v;
-        }
-    }
-}
 
 // --------------------------------------------------------------------------------------------
 // Sec. 2.3: the per-period winner, re-summed in FP64 from the FP32 grid.
@@ -981,28 +273,6 @@ __global__ void logl0_kernel(const float *__restrict__ wy, const float *__restri
 // Batched form: many light curves in one launch per stage.
 
 // Index of the curve owning item x of a CSR prefix array off[0..n] (off[c] <= x < off[c+1]).
-__device__ __forceinline__ int csr_find(const int64_t *__restrict__ off, int n, int64_t x) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-// Period k of a batch curve: pmin * ratio^k, ratio^k by LSB-first square-and-multiply.
-__device__ __forceinline__ double batch_period(double pmin, double ratio, int64_t k) {
-    double x = 1.0, b = ratio;
-    while (k) {
-        if (k & 1) x = __dmul_rn(x, b);
-        b = __dmul_rn(b, b);
-        k >>= 1;
-    }
-    return __dmul_rn(pmin, x);
-}
 
 // Sec. 2.1.1 for every point of every curve (curve found from the point index).
 __global__ void batch_resample_kernel(const double *__restrict__ time,
@@ -1050,59 +320,6 @@ batch_linear_kernel(const int64_t *__restrict__ tile_off, int n_curves,
                                    wy + cv.grid_off, w + cv.grid_off, cv.n_grid, tables, win_a,
                                    win_padlen, win_off, p, q, cv.I, cv.ld, kc_max,
                                    ab + cv.ab_off, nullptr, nullptr, nullptr);
-}
-
-// Sec. 2.3 for every curve: persistent blocks drain a queue of (curve, group of FT_G
-// periods) items; each group's best per period goes into the curve's key
-// (LR bits, inverted period index: the largest LR wins, ties to the smallest period index).
-template <bool KAHAN, int R>
-__global__ void __launch_bounds__(FT_THREADS, FT_MIN_BLOCKS)
-batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
-                  const int64_t *__restrict__ group_off, int n_curves, int64_t n_items, int J,
-                  const double *__restrict__ durations, double c, int64_t p, int64_t q,
-                  int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
-                  unsigned long long *__restrict__ curve_keys, int *__restrict__ status,
-                  const int64_t *__restrict__ item_list,
-                  const unsigned long long *__restrict__ n_items_dev) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // the queue length: n_items, or the count a device-side selection left (capped by n_items)
-    if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
-    float2 *strips = reinterpret_cast<float2 *>(smem_raw);
-    int32_t *tab = reinterpret_cast<int32_t *>(strips + FT_NSTAGE * FT_STRIP);
-    __shared__ fold_smem sm;
-    __shared__ int s_item;
-    const int t = threadIdx.x;
-    fold_init_barriers(sm);
-    ring iss, con;
-    for (;;) {
-        __syncthreads();  // the previous item is done with the shared state
-        if (t == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        if (s_item >= n_items) break;
-        // queue position -> work item: the position itself, or the caller's list entry
-        const int64_t item = item_list ? item_list[s_item] : (int64_t)s_item;
-        const int cidx = csr_find(group_off, n_curves, item);
-        const batch_curve cv = curves[cidx];
-        const int k0 = (int)(item - group_off[cidx]) * FT_G;
-        if (t < FT_G) {
-            const bool present = k0 + t < cv.n_periods;
-            fold_slot_meta(sm, t, present, present ? batch_period(cv.pmin, cv.ratio, k0 + t) : 0.0,
-                           cv.I, c, p, q);
-        }
-        if (!fold_group<KAHAN, R>(sm, strips, tab, ab + cv.ab_off, cv.I, cv.ld, J, durations,
-                                  nullptr, 0, iss, con, status))
-            return;  // uniform
-        for (int g = 0; g < FT_G; ++g) {
-            const unsigned long long v = block_max_key(sm.best[g][t], sm.red);
-            if (t == 0 && k0 + g < cv.n_periods) {
-                period_keys[cv.per_off + k0 + g] = v;
-                if (v != 0ull)
-                    atomicMax(&curve_keys[cidx],
-                              (v & 0xFFFFFFFF00000000ull) |
-                                  (unsigned long long)(0xFFFFFFFFu - (uint32_t)(k0 + g)));
-            }
-        }
-    }
 }
 
 // The winner of every curve: its best period from the curve key, that period's best
@@ -1358,10 +575,6 @@ __global__ void wait_timeout_selftest_kernel(int *out, int *status) {
 
 }  // namespace
 
-size_t fold_smem_bytes() {
-    return (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2) + (size_t)FT_TABLE * sizeof(int32_t);
-}
-
 // ============================================================================================
 // launchers
 
@@ -1401,13 +614,7 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
                                              (int)plan->lin_smem);
         if (e != cudaSuccess) return e;
     }
-    // the fold's strip ring and offset table (dynamic) exceed the default 48 KiB
-    for (auto fn : {fold_tma_kernel<false>, fold_tma_kernel<true>}) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)fold_smem_bytes());
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return fold_configure();
 }
 
 cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
@@ -1426,21 +633,6 @@ cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *w
         (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, plan->d_lin_order, ab, depth, var,
         dlogl);
     prof_mark(ctx, KID_LINEAR, false);
-    ctx->launches++;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
-                        const double *periods, int K, const uint8_t *mask,
-                        unsigned long long *keys, int *status) {
-    if (K <= 0) return cudaSuccess;
-    const int ngroups = (K + FT_G - 1) / FT_G;
-    prof_mark(ctx, KID_FOLD, true);
-    auto kern = plan->precision == CETRA_FP32_KAHAN ? fold_tma_kernel<true> : fold_tma_kernel<false>;
-    kern<<<ngroups, FT_THREADS, fold_smem_bytes(), ctx->stream>>>(
-        ab, (int)plan->n_t0, plan->ab_ld, plan->J, plan->d_durations, periods, K, mask,
-        plan->cadence, plan->p, plan->q, keys, status);
-    prof_mark(ctx, KID_FOLD, false);
     ctx->launches++;
     return cudaGetLastError();
 }
@@ -1520,28 +712,6 @@ cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int
     return cudaGetLastError();
 }
 
-// Fold variants the autotuner chooses from: phases per thread (FT_R or FT_R / 2).
-int batch_fold_variants() { return 2; }
-int batch_fold_blocks_per_sm(int) { return FT_MIN_BLOCKS; }
-
-cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
-                              const float2 *ab, const batch_curve *curves,
-                              const int64_t *group_off, int n_curves, int64_t n_items,
-                              int *queue, unsigned long long *period_keys,
-                              unsigned long long *curve_keys, int *status,
-                              const int64_t *item_list, const unsigned long long *n_items_dev) {
-    if (n_items <= 0) return cudaSuccess;
-    auto kern = batch_fold_kernel<false, FT_R>;
-    if (plan->precision == CETRA_FP32_KAHAN)
-        kern = batch_fold_kernel<true, FT_R / 2>;
-    else if (variant == 1)
-        kern = batch_fold_kernel<false, FT_R / 2>;
-    kern<<<blocks, FT_THREADS, fold_smem_bytes(), stream>>>(
-        ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
-        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list, n_items_dev);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_batch_finalize(cudaStream_t stream, const cetra_plan *plan, const float2 *ab,
                                   const batch_curve *curves, int n_curves,
                                   const unsigned long long *period_keys,
@@ -1574,13 +744,7 @@ cudaError_t batch_configure(const cetra_plan *plan) {
                                              (int)lin_max);
         if (e != cudaSuccess) return e;
     }
-    for (auto fn : {batch_fold_kernel<false, FT_R>, batch_fold_kernel<false, FT_R / 2>,
-                    batch_fold_kernel<true, FT_R / 2>}) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)fold_smem_bytes());
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return fold_configure();
 }
 
 cudaError_t launch_batch_features(cudaStream_t stream, int num_sms, const cetra_plan *plan,
