@@ -113,6 +113,15 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// The same copy to a 32-bit shared-memory address.
+__device__ __forceinline__ void bulk_load_s(uint32_t dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 // Potentially blocking test of a barrier phase: the thread may be suspended (up
 // to the hinted time) instead of spinning, so waiting warps do not take issue slots.
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
@@ -122,6 +131,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity), "r"(FT_SUSPEND_NS)
+        : "memory");
+    return ok != 0;
+}
+// Non-blocking test of a barrier phase (acquire: reads after a true result see the data).
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }

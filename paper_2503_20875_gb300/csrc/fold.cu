@@ -13,13 +13,15 @@
 // period reads its cells from there.
 //
 // Block: FT_THREADS consumer threads and one producer warp. The producer issues the bulk
-// copies into a ring of FT_NSTAGE strips; each strip has a "full" barrier (completed by the
-// copy's byte count) and an "empty" barrier (completed when every consumer thread has read
-// it). Consumers wait only for the strip they read next, so there is no block-wide barrier
-// per epoch; warps drift freely and the shared-memory pipe stays busy. Consumer thread c owns
-// phases i0 + c + r FT_THREADS (r < R) of every period of the sub-group being folded and
-// keeps their (A, B) sums in registers: one 8-byte shared load and one packed FP32 add per
-// cell read.
+// copies into a ring of strips in shared memory; each strip has a "full" barrier (completed
+// by the copy's byte count) and an "empty" barrier (completed when every consumer thread has
+// read it). Consumers wait only for the strip they read next, so there is no block-wide
+// barrier per epoch; warps drift freely and the shared-memory pipe stays busy. The ring's
+// strips are as long as the sub-group being folded needs (a tile plus the widest spread of its
+// offsets), so narrow groups get up to FT_NSTAGE strips in flight. Consumer thread c owns
+// phases i0 + c + r FT_THREADS (r < R) of every period of the sub-group and keeps their
+// (A, B) sums in registers as packed FP32 pairs: one 8-byte shared load and one packed add
+// per cell read.
 //
 // Epoch table: per sub-group the epoch offsets are computed once in FP64 into shared memory
 // as u16 byte offsets of each period's first cell within the epoch's strip, plus the
@@ -42,11 +44,32 @@
 
 namespace {
 
-// 8-byte shared-memory load at a 32-bit shared address.
-__device__ __forceinline__ float2 lds2(uint32_t addr) {
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+// One (A, B) cell as a packed FP32 pair (A in the low half), loaded from a 32-bit shared
+// address; sums stay packed, so no register moves are needed around the packed adds.
+__device__ __forceinline__ uint64_t lds_pair(uint32_t addr) {
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
     return v;
+}
+
+// acc += v on packed FP32 pairs.
+__device__ __forceinline__ void add_pair(uint64_t &acc, uint64_t v) {
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(v));
+}
+
+// Kahan-compensated s += v on packed pairs; nc holds minus the running compensation:
+// y = v + nc, t = s + y, nc = y - (t - s), s = t.
+__device__ __forceinline__ void kahan_add_pair(uint64_t &s, uint64_t &nc, uint64_t v) {
+    uint64_t y, t, d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(y) : "l"(v), "l"(nc));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(s), "l"(y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(t), "l"(s));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(nc) : "l"(y), "l"(d));
+    s = t;
+}
+
+__device__ __forceinline__ void split_pair(uint64_t v, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
 }
 
 // Block-wide barrier that threads may reach from different call sites (the producer warp and
@@ -58,12 +81,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// The epoch-0 cell of every period is its phase cell (o_0 = 0), so epoch 0 is shared.
-// Candidate test of the epilogue: 2 LR = x^2 / y exceeds the running best b only if
-// (x (1 + 2^-15)) x > b y. The exact comparison (x * __fdividef(x, y) > b) has a relative
-// error below 2^-21 and each product here one rounding, so the test never rejects a window
-// the exact comparison would take; the exact comparison then decides, as before.
-constexpr float kCandidate = 1.0f + 1.0f / 32768.0f;
+// Candidate test of the epilogue: the exact comparison of a window's 2 LR = x^2 / y with the
+// running best b is x * __fdividef(x, y) > b, whose left side has a relative error below
+// 2^-21. With h = b (1 - 2^-14) rounded once, x^2 > h y (each product rounded once) holds
+// whenever the exact comparison does (for b <= 0 trivially, for b > 0 by the margin), so a
+// tile in which no window passes it has no new maximum; otherwise the exact comparison runs
+// over the tile's windows in order, and decides as before.
+constexpr float kCandidate = 1.0f - 1.0f / 16384.0f;
 
 // Shared state of a fold block.
 struct fold_smem {
@@ -73,19 +97,25 @@ struct fold_smem {
     double P[FT_G], Ps[FT_G];        // period (days) and period in t0 steps
     int nph[FT_G], E[FT_G];          // phases, and an upper bound on the epochs with o_e < I
     int bad, tight;                  // table votes: spread too wide for the main / sliced path
+    int spread;                      // widest spread of the table's epochs (cells)
     int abort;                       // a bounded wait gave up: no more waits or copies
 };
 
-// Copies issued (producer) or consumed (consumers): copy n uses strip n % FT_NSTAGE and
-// completes phase n / FT_NSTAGE of that strip's barriers.
+// The strip ring as both sides see it. A sub-group uses ns strips of `bytes` each; strip s
+// has been filled f_s times so far, and bit s of `par` is f_s mod 2: its next fill completes
+// phase parity (par >> s) & 1 of full[s] and needs phase f_s - 1 of empty[s] to be complete.
+// The producer and every consumer step through the same sequence of strips.
 struct ring {
-    uint32_t n = 0, stage = 0, parity = 0;
+    uint32_t stage = 0, ns = 1, bytes = 0, par = 0;
+    __device__ __forceinline__ void start(uint32_t nstages, uint32_t stage_bytes) {
+        stage = 0;
+        ns = nstages;
+        bytes = stage_bytes;
+    }
+    __device__ __forceinline__ uint32_t parity() const { return (par >> stage) & 1u; }
     __device__ __forceinline__ void next() {
-        ++n;
-        if (++stage == FT_NSTAGE) {
-            stage = 0;
-            parity ^= 1u;
-        }
+        par ^= 1u << stage;
+        stage = stage + 1 == ns ? 0u : stage + 1;
     }
 };
 
@@ -160,17 +190,23 @@ __device__ __forceinline__ unsigned period_use(const fold_smem &sm, int g0, doub
 // (false if any lane's wait gave up, or if the phase is not complete and the block has
 // aborted). A wait that gives up records the time-out and aborts the block; the finalize
 // kernel then writes NaN for every period.
-__device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t parity,
-                                          int *status) {
-    bool ok = mbar_try(bar, parity);
-    if (!ok && !*(volatile int *)&sm.abort) {
-        ok = mbar_wait(bar, parity);
-        if (!ok) {
+__device__ __noinline__ bool fold_wait_slow(fold_smem &sm, uint64_t *bar, uint32_t parity,
+                                            int *status) {
+    bool ok = true;
+    if (!mbar_test(bar, parity)) {
+        ok = !*(volatile int *)&sm.abort && mbar_wait(bar, parity);
+        if (!ok && !*(volatile int *)&sm.abort) {
             *(volatile int *)&sm.abort = 1;
             atomicExch(status, CETRA_ETIMEOUT);
         }
     }
     return __all_sync(0xFFFFFFFFu, ok);
+}
+
+__device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t parity,
+                                          int *status) {
+    if (__all_sync(0xFFFFFFFFu, mbar_test(bar, parity))) return true;  // the phase is complete
+    return fold_wait_slow(sm, bar, parity, status);
 }
 
 // Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
@@ -191,6 +227,17 @@ __device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float 
     }
 }
 
+// Exact running maximum over one window sum (x, y) = (sum A, sum B) at flat index at:
+// 2 LR = x * (x / y); a null sum gives NaN, never a maximum; the first of equal values stays.
+__device__ __forceinline__ void take_max(float x, float y, uint32_t at, float &best_lr2,
+                                         uint32_t &best_at) {
+    const float lr2 = x * __fdividef(x, y);
+    if (lr2 > best_lr2) {
+        best_lr2 = lr2;
+        best_at = at;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Main path: tiles of T = FT_THREADS R phases, one strip per epoch.
 
@@ -202,10 +249,10 @@ __device__ __forceinline__ int live_epochs(const fold_table &tb, int nE, int I, 
 }
 
 template <int GS, int R>
-__device__ void produce_main(fold_smem &sm, float2 *strips, const fold_table &tb, int g0,
+__device__ void produce_main(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
                              int nph_sub, const float2 *__restrict__ ab, int I, int64_t ld, int J,
                              int jlo, int jhi, const double *__restrict__ durations,
-                             const uint8_t *__restrict__ mask, int mask_k0, ring &iss,
+                             const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
                              int *__restrict__ status) {
     constexpr int T = FT_THREADS * R;
     const bool leader = (threadIdx.x & 31) == 0;
@@ -216,33 +263,66 @@ __device__ void produce_main(fold_smem &sm, float2 *strips, const fold_table &tb
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
             nE = live_epochs(tb, nE, I, i0);
             for (int e = 0; e < nE; ++e) {
-                if (!fold_wait(sm, &sm.empty[iss.stage], iss.parity ^ 1u, status)) return;
+                if (!fold_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u, status)) return;
                 if (leader) {
                     const int a = i0 + (tb.tmin[e] & ~1);
                     const int len = ((i0 + tb.tmax[e] + T - a) + 1) & ~1;
                     const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
                     fence_proxy_async();
-                    mbar_expect_tx(&sm.full[iss.stage], bytes);
-                    bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.full[iss.stage]);
+                    mbar_expect_tx(&sm.full[rg.stage], bytes);
+                    bulk_load_s(ring0 + rg.stage * rg.bytes, row + a, bytes, &sm.full[rg.stage]);
                 }
                 __syncwarp();
-                iss.next();
+                rg.next();
             }
         }
     }
 }
 
+// Epochs 1 .. nE-1 of a tile (epoch 0 initialised acc): ALL = every period of the sub-group
+// is folded at this duration (no per-period test in the loop).
+template <int GS, int R, bool KAHAN, bool ALL>
+__device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &tb, int nE,
+                                               unsigned use, uint32_t mine, uint64_t (&acc)[GS][R],
+                                               uint64_t (&cmp)[KAHAN ? GS : 1][KAHAN ? R : 1],
+                                               ring &rg, int *__restrict__ status) {
+    constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
+    for (int e = 1; e < nE; ++e) {
+        if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return false;
+        const uint32_t a = mine + rg.stage * rg.bytes;
+        packed_offsets<GS> off;
+        off.load(tb.off + e * GS);
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            if (!ALL && !((use >> gg) & 1u)) continue;
+            const uint32_t ag = a + off[gg];
+            uint64_t v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = lds_pair(ag + r * kRowStep);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if constexpr (KAHAN)
+                    kahan_add_pair(acc[gg][r], cmp[gg][r], v[r]);
+                else
+                    add_pair(acc[gg][r], v[r]);
+            }
+        }
+        mbar_arrive(&sm.empty[rg.stage]);
+        rg.next();
+    }
+    return true;
+}
+
 template <int GS, int R, bool KAHAN>
-__device__ void consume_main(fold_smem &sm, const float2 *strips, const fold_table &tb, int g0,
+__device__ void consume_main(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
                              int nph_sub, int I, int J, int jlo, int jhi,
                              const double *__restrict__ durations,
-                             const uint8_t *__restrict__ mask, int mask_k0, ring &con,
+                             const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
                              int *__restrict__ status) {
     constexpr int T = FT_THREADS * R;
-    constexpr uint32_t kStageBytes = FT_STRIP * (uint32_t)sizeof(float2);
     constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
     const int c = threadIdx.x;
-    const uint32_t mine = smem_u32(strips) + (uint32_t)c * (uint32_t)sizeof(float2);
+    const uint32_t mine = ring0 + (uint32_t)c * (uint32_t)sizeof(float2);
     float best_lr2[GS];
     uint32_t best_at[GS];
 #pragma unroll
@@ -261,17 +341,17 @@ __device__ void consume_main(fold_smem &sm, const float2 *strips, const fold_tab
         int nE = tb.Es;
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
             nE = live_epochs(tb, nE, I, i0);
-            float2 acc[GS][R];
-            float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
-            // epoch 0: every period's cell is its phase cell. (A wait that gave up ends the
-            // path at once: the main path has no block barrier, so every thread still meets the
-            // caller's next one.)
-            if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) return;
+            uint64_t acc[GS][R];
+            uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
+            // epoch 0: every period's cell is its phase cell (o_0 = 0). A wait that gave up
+            // ends the path at once: the main path has no block barrier, so every thread
+            // still meets the caller's next one.
+            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return;
             {
-                const uint32_t a = mine + con.stage * kStageBytes;
-                float2 v[R];
+                const uint32_t a = mine + rg.stage * rg.bytes;
+                uint64_t v[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = lds2(a + r * kRowStep);
+                for (int r = 0; r < R; ++r) v[r] = lds_pair(a + r * kRowStep);
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
@@ -280,53 +360,51 @@ __device__ void consume_main(fold_smem &sm, const float2 *strips, const fold_tab
 #pragma unroll
                     for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-                        for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+                        for (int r = 0; r < R; ++r) cmp[gg][r] = 0ull;
                 }
-                mbar_arrive(&sm.empty[con.stage]);
+                mbar_arrive(&sm.empty[rg.stage]);
             }
-            con.next();
-            for (int e = 1; e < nE; ++e) {
-                if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) return;
-                const uint32_t a = mine + con.stage * kStageBytes;
-                packed_offsets<GS> off;
-                off.load(tb.off + e * GS);
+            rg.next();
+            const bool ok =
+                all_used
+                    ? consume_epochs<GS, R, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg, status)
+                    : consume_epochs<GS, R, KAHAN, false>(sm, tb, nE, use, mine, acc, cmp, rg, status);
+            if (!ok) return;
+            // 2 LR = SA^2 / SB per (period, phase); the running maximum keeps the first
+            // (smallest j, then smallest i) of equal values. Whole tiles first run the
+            // candidate test over all their windows.
+            const bool whole = i0 + T <= nmin;
+            bool any = !whole;
+            if (whole) {
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     if (!all_used && !((use >> gg) & 1u)) continue;
-                    const uint32_t ag = a + off[gg];
-                    float2 v[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = lds2(ag + r * kRowStep);
+                    const float h = best_lr2[gg] * kCandidate;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        if constexpr (KAHAN)
-                            kahan_add2(acc[gg][r], cmp[gg][r], v[r]);
-                        else
-                            add2(acc[gg][r], v[r]);
+                        uint64_t v = acc[gg][r];
+                        if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
+                        float x, y;
+                        split_pair(v, x, y);
+                        any |= x * x > h * y;
                     }
                 }
-                mbar_arrive(&sm.empty[con.stage]);
-                con.next();
             }
-            // 2 LR = SA^2 / SB per (period, phase); a null sum gives NaN, never a maximum;
-            // the running maximum keeps the first (smallest j, then smallest i) of equal values
-            const bool whole = i0 + T <= nmin;
+            if (any) {
 #pragma unroll
-            for (int gg = 0; gg < GS; ++gg) {
-                if (!((use >> gg) & 1u)) continue;
-                const int nph = sm.nph[g0 + gg];
+                for (int gg = 0; gg < GS; ++gg) {
+                    if (!((use >> gg) & 1u)) continue;
+                    const int nph = sm.nph[g0 + gg];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = i0 + c + r * FT_THREADS;
-                    float2 v = acc[gg][r];
-                    if constexpr (KAHAN) add2(v, cmp[gg][r]);
-                    if (!whole && i >= nph) continue;
-                    if ((v.x * kCandidate) * v.x > best_lr2[gg] * v.y) {
-                        const float lr2 = v.x * __fdividef(v.x, v.y);
-                        if (lr2 > best_lr2[gg]) {
-                            best_lr2[gg] = lr2;
-                            best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)i;
-                        }
+                    for (int r = 0; r < R; ++r) {
+                        const int i = i0 + c + r * FT_THREADS;
+                        uint64_t v = acc[gg][r];
+                        if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
+                        float x, y;
+                        split_pair(v, x, y);
+                        if (i < nph)
+                            take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)i, best_lr2[gg],
+                                     best_at[gg]);
                     }
                 }
             }
@@ -342,7 +420,7 @@ __device__ void consume_main(fold_smem &sm, const float2 *strips, const fold_tab
 // e = s H + h of super-epoch s, one strip per super-epoch. The H partial sums of a phase are
 // then added in slice order through shared memory. (Strip bound: tmin grows by at most Tp
 // per epoch, since o_{e+1} - o_e <= ceil(Ps) <= Tp for the period that attains tmin[e], so a
-// super-epoch needs at most H Tp + spread + 2 <= T + spread + 2 cells; the table check keeps
+// super-epoch needs at most H Tp + spread + 3 <= T + spread + 3 cells; the table check keeps
 // spread <= FT_STRIP - T - 8 for this path.)
 
 __device__ __forceinline__ bool live_epoch(const fold_table &tb, int e, int I) {
@@ -350,10 +428,10 @@ __device__ __forceinline__ bool live_epoch(const fold_table &tb, int e, int I) {
 }
 
 template <int GS, int R>
-__device__ void produce_sliced(fold_smem &sm, float2 *strips, const fold_table &tb, int g0,
+__device__ void produce_sliced(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
                                int Tp, const float2 *__restrict__ ab, int I, int64_t ld, int J,
                                int jlo, int jhi, const double *__restrict__ durations,
-                               const uint8_t *__restrict__ mask, int mask_k0, ring &iss,
+                               const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
                                int *__restrict__ status) {
     constexpr int T = FT_THREADS * R;
     const int H = T / Tp;
@@ -363,7 +441,8 @@ __device__ void produce_sliced(fold_smem &sm, float2 *strips, const fold_table &
         if (!use) continue;
         const float2 *row = ab + (int64_t)j * ld;
         for (int s = 0; live_epoch(tb, s * H, I); ++s) {
-            const bool ok = fold_wait(sm, &sm.empty[iss.stage], iss.parity ^ 1u, status);
+            // (after an abort this only keeps the loop, and the barriers below, in step)
+            const bool ok = fold_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u, status);
             if (leader && ok) {
                 const int e0 = s * H;
                 const int a = tb.tmin[e0] & ~1;
@@ -373,11 +452,11 @@ __device__ void produce_sliced(fold_smem &sm, float2 *strips, const fold_table &
                 const int len = ((end - a) + 1) & ~1;
                 const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
                 fence_proxy_async();
-                mbar_expect_tx(&sm.full[iss.stage], bytes);
-                bulk_load(strips + iss.stage * FT_STRIP, row + a, bytes, &sm.full[iss.stage]);
+                mbar_expect_tx(&sm.full[rg.stage], bytes);
+                bulk_load_s(ring0 + rg.stage * rg.bytes, row + a, bytes, &sm.full[rg.stage]);
             }
             __syncwarp();
-            iss.next();
+            rg.next();
         }
         // the consumers' slice reduction: two block barriers per folded period
         for (int gg = 0; gg < GS; ++gg)
@@ -389,16 +468,14 @@ __device__ void produce_sliced(fold_smem &sm, float2 *strips, const fold_table &
 }
 
 template <int GS, int R, bool KAHAN>
-__device__ void consume_sliced(fold_smem &sm, const float2 *strips, float2 *part,
+__device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part,
                                const fold_table &tb, int g0, int Tp, int I, int J, int jlo,
                                int jhi, const double *__restrict__ durations,
-                               const uint8_t *__restrict__ mask, int mask_k0, ring &con,
+                               const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
                                int *__restrict__ status) {
     constexpr int T = FT_THREADS * R;
-    constexpr uint32_t kStageBytes = FT_STRIP * (uint32_t)sizeof(float2);
     const int H = T / Tp;
     const int c = threadIdx.x;
-    const uint32_t base0 = smem_u32(strips);
     int slice[R], phase[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -417,25 +494,26 @@ __device__ void consume_sliced(fold_smem &sm, const float2 *strips, float2 *part
         const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
         if (!use) continue;
         const bool all_used = use == (1u << GS) - 1u;
-        float2 acc[GS][R];
-        float2 cmp[KAHAN ? GS : 1][KAHAN ? R : 1];
+        uint64_t acc[GS][R];
+        uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[gg][r] = make_float2(0.f, 0.f);
+            for (int r = 0; r < R; ++r) acc[gg][r] = 0ull;
         if constexpr (KAHAN) {
 #pragma unroll
             for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-                for (int r = 0; r < R; ++r) cmp[gg][r] = make_float2(0.f, 0.f);
+                for (int r = 0; r < R; ++r) cmp[gg][r] = 0ull;
         }
         for (int s = 0; live_epoch(tb, s * H, I); ++s) {
-            if (!fold_wait(sm, &sm.full[con.stage], con.parity, status)) {
-                con.next();
+            // after an abort the loop runs on without work, to keep the barriers below in step
+            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) {
+                rg.next();
                 continue;
             }
             const int a_s = tb.tmin[s * H] & ~1;
-            const uint32_t stage = base0 + con.stage * kStageBytes;
+            const uint32_t stage = ring0 + rg.stage * rg.bytes;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (slice[r] >= H) continue;  // lane past the last whole slice
@@ -448,15 +526,15 @@ __device__ void consume_sliced(fold_smem &sm, const float2 *strips, float2 *part
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     if (!all_used && !((use >> gg) & 1u)) continue;
-                    const float2 v = lds2(lb + off[gg]);
+                    const uint64_t v = lds_pair(lb + off[gg]);
                     if constexpr (KAHAN)
-                        kahan_add2(acc[gg][r], cmp[gg][r], v);
+                        kahan_add_pair(acc[gg][r], cmp[gg][r], v);
                     else
-                        add2(acc[gg][r], v);
+                        add_pair(acc[gg][r], v);
                 }
             }
-            mbar_arrive(&sm.empty[con.stage]);
-            con.next();
+            mbar_arrive(&sm.empty[rg.stage]);
+            rg.next();
         }
         // the slices' partial sums of each phase, added in slice order
 #pragma unroll
@@ -464,20 +542,20 @@ __device__ void consume_sliced(fold_smem &sm, const float2 *strips, float2 *part
             if (!((use >> gg) & 1u)) continue;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float2 v = acc[gg][r];
-                if constexpr (KAHAN) add2(v, cmp[gg][r]);
+                uint64_t v = acc[gg][r];
+                if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
                 part[c + r * FT_THREADS] = v;
             }
             block_sync();
             const int nph = sm.nph[g0 + gg];
             for (int phi = c; phi < Tp; phi += FT_THREADS) {
-                float2 v = part[phi];
-                for (int h = 1; h < H; ++h) add2(v, part[h * Tp + phi]);
-                const float lr2 = v.x * __fdividef(v.x, v.y);
-                if (phi < nph && v.y > 0.0f && lr2 > best_lr2[gg]) {
-                    best_lr2[gg] = lr2;
-                    best_at[gg] = (uint32_t)j * (uint32_t)I + (uint32_t)phi;
-                }
+                uint64_t v = part[phi];
+                for (int h = 1; h < H; ++h) add_pair(v, part[h * Tp + phi]);
+                float x, y;
+                split_pair(v, x, y);
+                if (phi < nph && y > 0.0f)
+                    take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)phi, best_lr2[gg],
+                             best_at[gg]);
             }
             block_sync();
         }
@@ -557,6 +635,7 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
     int32_t *tmin = reinterpret_cast<int32_t *>(raw + table_off_bytes(Es, GS));
     int32_t *tmax = tmin + Es;
     bool bad = false, tight = false;
+    int64_t widest = 0;
     for (int e = threadIdx.x; e < Es; e += blockDim.x) {
         int64_t o[GS];
         int64_t mn = INT64_MAX, mx = INT64_MIN;
@@ -576,6 +655,7 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
         const int64_t spread = mx - mn;
         if (spread > FT_STRIP - T - 2) bad = true;
         if (spread > FT_STRIP - T - 8) tight = true;
+        widest = spread > widest ? spread : widest;
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg) {
             const int64_t d = o[gg] >= 0 ? (o[gg] - base) * (int64_t)sizeof(float2) : 0;
@@ -586,10 +666,11 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
     }
     if (bad) sm.bad = 1;
     if (tight) sm.tight = 1;
+    if (!bad && widest > 0) atomicMax(&sm.spread, (int)widest);
 }
 
 template <int GS, int R, bool KAHAN>
-__device__ void fold_subgroup(fold_smem &sm, float2 *strips, const fold_table &tb, float2 *part,
+__device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &tb, uint64_t *part,
                               bool sliced, int Tp, int g0, int nph_sub,
                               const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
                               int jhi, const double *__restrict__ durations,
@@ -598,16 +679,16 @@ __device__ void fold_subgroup(fold_smem &sm, float2 *strips, const fold_table &t
     const bool producer = threadIdx.x >= FT_THREADS;
     if (sliced) {
         if (producer)
-            produce_sliced<GS, R>(sm, strips, tb, g0, Tp, ab, I, ld, J, jlo, jhi, durations, mask,
+            produce_sliced<GS, R>(sm, ring0, tb, g0, Tp, ab, I, ld, J, jlo, jhi, durations, mask,
                                   mask_k0, rg, status);
         else
-            consume_sliced<GS, R, KAHAN>(sm, strips, part, tb, g0, Tp, I, J, jlo, jhi, durations,
+            consume_sliced<GS, R, KAHAN>(sm, ring0, part, tb, g0, Tp, I, J, jlo, jhi, durations,
                                          mask, mask_k0, rg, status);
     } else if (producer) {
-        produce_main<GS, R>(sm, strips, tb, g0, nph_sub, ab, I, ld, J, jlo, jhi, durations, mask,
+        produce_main<GS, R>(sm, ring0, tb, g0, nph_sub, ab, I, ld, J, jlo, jhi, durations, mask,
                             mask_k0, rg, status);
     } else {
-        consume_main<GS, R, KAHAN>(sm, strips, tb, g0, nph_sub, I, J, jlo, jhi, durations, mask,
+        consume_main<GS, R, KAHAN>(sm, ring0, tb, g0, nph_sub, I, J, jlo, jhi, durations, mask,
                                    mask_k0, rg, status);
     }
 }
@@ -617,7 +698,7 @@ __device__ void fold_subgroup(fold_smem &sm, float2 *strips, const fold_table &t
 // best key ends in sm.best[g]. Mask rows are (mask_k0 + g). A wait that gave up leaves
 // sm.abort set.
 template <bool KAHAN, int R>
-__device__ void fold_group(fold_smem &sm, float2 *strips, unsigned char *tab, float2 *part,
+__device__ void fold_group(fold_smem &sm, uint32_t ring0, unsigned char *tab, uint64_t *part,
                            const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
                            int jhi, const double *__restrict__ durations,
                            const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
@@ -640,7 +721,7 @@ __device__ void fold_group(fold_smem &sm, float2 *strips, unsigned char *tab, fl
                 break;  // a single period with too many epochs: no table
             }
             block_sync();  // everyone is done with the previous table
-            if (threadIdx.x == 0) sm.bad = sm.tight = 0;
+            if (threadIdx.x == 0) sm.bad = sm.tight = sm.spread = 0;
             block_sync();
             if (GS == 8)
                 build_table<8>(sm, tab, g0, Es, T);
@@ -674,17 +755,22 @@ __device__ void fold_group(fold_smem &sm, float2 *strips, unsigned char *tab, fl
         const fold_table tb = table_view(tab, Es, GS);
         const int Tp = max(32, nph_sub);  // phases per epoch slice
         const bool sliced = !sm.tight && 2 * Tp <= T;
+        // strips as long as this sub-group's copies can be (a tile plus the widest spread,
+        // rounded to whole 16-byte units), as many as the ring holds
+        const uint32_t stage_bytes =
+            (uint32_t)((T + sm.spread + 5) & ~1) * (uint32_t)sizeof(float2);
+        rg.start(min((uint32_t)FT_NSTAGE, (uint32_t)FT_RING_BYTES / stage_bytes), stage_bytes);
         if (GS == 8)
-            fold_subgroup<8, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<8, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else if (GS == 4)
-            fold_subgroup<4, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<4, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else if (GS == 2)
-            fold_subgroup<2, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<2, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else
-            fold_subgroup<1, R, KAHAN>(sm, strips, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<1, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         g0 += GS;
     }
@@ -703,21 +789,19 @@ __device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
     }
 }
 
-// A block that aborted: the producer waits (bounded) for the copies it may still have in
-// flight, the last FT_NSTAGE it issued, so that none lands in shared memory after the block
-// exits.
+// A block that aborted: the producer waits (bounded) for the last fill of every strip to
+// land, so that no copy lands in shared memory after the block exits. (A strip never filled
+// has parity bit 0: its wait on phase parity 1 passes at once.)
 __device__ void drain_copies(fold_smem &sm, const ring &rg) {
     if (threadIdx.x < FT_THREADS) return;
-    const uint32_t first = rg.n > FT_NSTAGE ? rg.n - FT_NSTAGE : 0u;
-    for (uint32_t n = first; n < rg.n; ++n)
-        mbar_wait(&sm.full[n % FT_NSTAGE], (n / FT_NSTAGE) & 1u);
+    for (int s = 0; s < FT_NSTAGE; ++s) mbar_wait(&sm.full[s], ((rg.par >> s) & 1u) ^ 1u);
 }
 
-__device__ __forceinline__ void fold_smem_views(unsigned char *raw, float2 *&strips,
-                                                unsigned char *&tab, float2 *&part) {
-    strips = reinterpret_cast<float2 *>(raw);
-    tab = raw + (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2);
-    part = reinterpret_cast<float2 *>(tab + FT_TAB_BYTES);
+__device__ __forceinline__ void fold_smem_views(unsigned char *raw, uint32_t &ring0,
+                                                unsigned char *&tab, uint64_t *&part) {
+    ring0 = smem_u32(raw);
+    tab = raw + FT_RING_BYTES;
+    part = reinterpret_cast<uint64_t *>(tab + FT_TAB_BYTES);
 }
 
 // Single light curve. Work item = (duration chunk, group); chunks outermost so that the blocks
@@ -733,9 +817,10 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
             int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ fold_smem sm;
-    float2 *strips, *part;
+    uint32_t ring0;
+    uint64_t *part;
     unsigned char *tab;
-    fold_smem_views(smem_raw, strips, tab, part);
+    fold_smem_views(smem_raw, ring0, tab, part);
     const int t = threadIdx.x;
     const int jc = blockIdx.x / n_groups;
     const int grp = n_groups - 1 - (int)(blockIdx.x % n_groups);
@@ -746,7 +831,7 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     block_sync();
     ring rg;
     constexpr int R = KAHAN ? FT_R / 2 : FT_R;
-    fold_group<KAHAN, R>(sm, strips, tab, part, ab, I, ld, J, jlo, jhi, durations, mask, k0, rg,
+    fold_group<KAHAN, R>(sm, ring0, tab, part, ab, I, ld, J, jlo, jhi, durations, mask, k0, rg,
                          status);
     block_sync();
     if (sm.abort) {
@@ -779,9 +864,10 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
     __shared__ int s_item;
     // the queue length: n_items, or the count a device-side selection left (capped by n_items)
     if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
-    float2 *strips, *part;
+    uint32_t ring0;
+    uint64_t *part;
     unsigned char *tab;
-    fold_smem_views(smem_raw, strips, tab, part);
+    fold_smem_views(smem_raw, ring0, tab, part);
     const int t = threadIdx.x;
     fold_init_barriers(sm);
     ring rg;
@@ -801,7 +887,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                            cv.I, c, p, q);
         }
         block_sync();
-        fold_group<KAHAN, R>(sm, strips, tab, part, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
+        fold_group<KAHAN, R>(sm, ring0, tab, part, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
                              durations, nullptr, 0, rg, status);
         block_sync();
         if (sm.abort) {
@@ -821,8 +907,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
 }  // namespace
 
 size_t fold_smem_bytes() {
-    return (size_t)FT_NSTAGE * FT_STRIP * sizeof(float2) + (size_t)FT_TAB_BYTES +
-           (size_t)FT_T * sizeof(float2);
+    return (size_t)FT_RING_BYTES + (size_t)FT_TAB_BYTES + (size_t)FT_T * sizeof(uint64_t);
 }
 
 cudaError_t fold_configure() {
