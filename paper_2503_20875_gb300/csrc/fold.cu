@@ -57,6 +57,13 @@ __device__ __forceinline__ void add_pair(uint64_t &acc, uint64_t v) {
     asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(v));
 }
 
+// a + b on packed FP32 pairs.
+__device__ __forceinline__ uint64_t sum_pair(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Kahan-compensated s += v on packed pairs; nc holds minus the running compensation:
 // y = v + nc, t = s + y, nc = y - (t - s), s = t.
 __device__ __forceinline__ void kahan_add_pair(uint64_t &s, uint64_t &nc, uint64_t v) {
@@ -211,13 +218,18 @@ __device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t
 
 // Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
 // slot's best key in shared memory.
+// The flat index of each thread's best window of period slot g is kept in shared memory,
+// best_at[g * FT_THREADS + c]: it is written only when a maximum changes, so it need not take
+// registers in the hot loop.
 template <int GS>
 __device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float *best_lr2,
                                              const uint32_t *best_at) {
+    const int c = threadIdx.x;
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
         unsigned long long key =
-            best_lr2[gg] >= 0.0f ? make_key(0.5f * best_lr2[gg], best_at[gg]) : 0ull;
+            best_lr2[gg] >= 0.0f ? make_key(0.5f * best_lr2[gg], best_at[gg * FT_THREADS + c])
+                                 : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, key, o);
@@ -230,11 +242,11 @@ __device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float 
 // Exact running maximum over one window sum (x, y) = (sum A, sum B) at flat index at:
 // 2 LR = x * (x / y); a null sum gives NaN, never a maximum; the first of equal values stays.
 __device__ __forceinline__ void take_max(float x, float y, uint32_t at, float &best_lr2,
-                                         uint32_t &best_at) {
+                                         uint32_t *best_at) {
     const float lr2 = x * __fdividef(x, y);
     if (lr2 > best_lr2) {
         best_lr2 = lr2;
-        best_at = at;
+        *best_at = at;
     }
 }
 
@@ -279,15 +291,15 @@ __device__ void produce_main(fold_smem &sm, uint32_t ring0, const fold_table &tb
     }
 }
 
-// Epochs 1 .. nE-1 of a tile (epoch 0 initialised acc): ALL = every period of the sub-group
-// is folded at this duration (no per-period test in the loop).
+// Epochs 2 .. nE-1 of a tile (epochs 0 and 1 initialised acc): ALL = every period of the
+// sub-group is folded at this duration (no per-period test in the loop).
 template <int GS, int R, bool KAHAN, bool ALL>
 __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &tb, int nE,
                                                unsigned use, uint32_t mine, uint64_t (&acc)[GS][R],
                                                uint64_t (&cmp)[KAHAN ? GS : 1][KAHAN ? R : 1],
                                                ring &rg, int *__restrict__ status) {
     constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
-    for (int e = 1; e < nE; ++e) {
+    for (int e = 2; e < nE; ++e) {
         if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return false;
         const uint32_t a = mine + rg.stage * rg.bytes;
         packed_offsets<GS> off;
@@ -314,9 +326,9 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
 }
 
 template <int GS, int R, bool KAHAN>
-__device__ void consume_main(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
-                             int nph_sub, int I, int J, int jlo, int jhi,
-                             const double *__restrict__ durations,
+__device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
+                             const fold_table &tb, int g0, int nph_sub, int I, int J, int jlo,
+                             int jhi, const double *__restrict__ durations,
                              const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
                              int *__restrict__ status) {
     constexpr int T = FT_THREADS * R;
@@ -324,11 +336,10 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, const fold_table &tb
     const int c = threadIdx.x;
     const uint32_t mine = ring0 + (uint32_t)c * (uint32_t)sizeof(float2);
     float best_lr2[GS];
-    uint32_t best_at[GS];
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
         best_lr2[gg] = -1.0f;
-        best_at[gg] = 0u;
+        best_at[gg * FT_THREADS + c] = 0u;
     }
     for (int j = jlo; j < jhi; ++j) {
         const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
@@ -343,28 +354,53 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, const fold_table &tb
             nE = live_epochs(tb, nE, I, i0);
             uint64_t acc[GS][R];
             uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
-            // epoch 0: every period's cell is its phase cell (o_0 = 0). A wait that gave up
-            // ends the path at once: the main path has no block barrier, so every thread
-            // still meets the caller's next one.
+            // Epoch 0: every period's cell is its phase cell (o_0 = 0), one load for all.
+            // Epoch 1 then starts each sum as (epoch-0 cell + epoch-1 cell). (A wait that gave
+            // up ends the path at once: the main path has no block barrier, so every thread
+            // still meets the caller's next one.)
             if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return;
+            uint64_t v0[R];
             {
                 const uint32_t a = mine + rg.stage * rg.bytes;
-                uint64_t v[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = lds_pair(a + r * kRowStep);
+                for (int r = 0; r < R; ++r) v0[r] = lds_pair(a + r * kRowStep);
+                mbar_arrive(&sm.empty[rg.stage]);
+            }
+            rg.next();
+            if (KAHAN || nE < 2) {
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[gg][r] = v[r];
+                    for (int r = 0; r < R; ++r) acc[gg][r] = v0[r];
                 if constexpr (KAHAN) {
 #pragma unroll
                     for (int gg = 0; gg < GS; ++gg)
 #pragma unroll
                         for (int r = 0; r < R; ++r) cmp[gg][r] = 0ull;
                 }
-                mbar_arrive(&sm.empty[rg.stage]);
             }
-            rg.next();
+            if (nE >= 2) {
+                if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return;
+                const uint32_t a = mine + rg.stage * rg.bytes;
+                packed_offsets<GS> off;
+                off.load(tb.off + GS);
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg) {
+                    const uint32_t ag = a + off[gg];
+                    uint64_t v[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = lds_pair(ag + r * kRowStep);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if constexpr (KAHAN)
+                            kahan_add_pair(acc[gg][r], cmp[gg][r], v[r]);
+                        else
+                            acc[gg][r] = sum_pair(v0[r], v[r]);
+                    }
+                }
+                mbar_arrive(&sm.empty[rg.stage]);
+                rg.next();
+            }
             const bool ok =
                 all_used
                     ? consume_epochs<GS, R, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg, status)
@@ -404,7 +440,7 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, const fold_table &tb
                         split_pair(v, x, y);
                         if (i < nph)
                             take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)i, best_lr2[gg],
-                                     best_at[gg]);
+                                     &best_at[gg * FT_THREADS + c]);
                     }
                 }
             }
@@ -468,7 +504,7 @@ __device__ void produce_sliced(fold_smem &sm, uint32_t ring0, const fold_table &
 }
 
 template <int GS, int R, bool KAHAN>
-__device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part,
+__device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, uint32_t *best_at,
                                const fold_table &tb, int g0, int Tp, int I, int J, int jlo,
                                int jhi, const double *__restrict__ durations,
                                const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
@@ -484,11 +520,10 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part,
         phase[r] = L - slice[r] * Tp;
     }
     float best_lr2[GS];
-    uint32_t best_at[GS];
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
         best_lr2[gg] = -1.0f;
-        best_at[gg] = 0u;
+        best_at[gg * FT_THREADS + c] = 0u;
     }
     for (int j = jlo; j < jhi; ++j) {
         const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
@@ -555,7 +590,7 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part,
                 split_pair(v, x, y);
                 if (phi < nph && y > 0.0f)
                     take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)phi, best_lr2[gg],
-                             best_at[gg]);
+                             &best_at[gg * FT_THREADS + c]);
             }
             block_sync();
         }
@@ -671,7 +706,7 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
 
 template <int GS, int R, bool KAHAN>
 __device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &tb, uint64_t *part,
-                              bool sliced, int Tp, int g0, int nph_sub,
+                              uint32_t *best_at, bool sliced, int Tp, int g0, int nph_sub,
                               const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
                               int jhi, const double *__restrict__ durations,
                               const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
@@ -682,14 +717,14 @@ __device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &t
             produce_sliced<GS, R>(sm, ring0, tb, g0, Tp, ab, I, ld, J, jlo, jhi, durations, mask,
                                   mask_k0, rg, status);
         else
-            consume_sliced<GS, R, KAHAN>(sm, ring0, part, tb, g0, Tp, I, J, jlo, jhi, durations,
-                                         mask, mask_k0, rg, status);
+            consume_sliced<GS, R, KAHAN>(sm, ring0, part, best_at, tb, g0, Tp, I, J, jlo, jhi,
+                                         durations, mask, mask_k0, rg, status);
     } else if (producer) {
         produce_main<GS, R>(sm, ring0, tb, g0, nph_sub, ab, I, ld, J, jlo, jhi, durations, mask,
                             mask_k0, rg, status);
     } else {
-        consume_main<GS, R, KAHAN>(sm, ring0, tb, g0, nph_sub, I, J, jlo, jhi, durations, mask,
-                                   mask_k0, rg, status);
+        consume_main<GS, R, KAHAN>(sm, ring0, best_at, tb, g0, nph_sub, I, J, jlo, jhi, durations,
+                                   mask, mask_k0, rg, status);
     }
 }
 
@@ -698,7 +733,7 @@ __device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &t
 // best key ends in sm.best[g]. Mask rows are (mask_k0 + g). A wait that gave up leaves
 // sm.abort set.
 template <bool KAHAN, int R>
-__device__ void fold_group(fold_smem &sm, uint32_t ring0, unsigned char *tab, uint64_t *part,
+__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab, uint32_t *best_at,
                            const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
                            int jhi, const double *__restrict__ durations,
                            const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
@@ -756,21 +791,25 @@ __device__ void fold_group(fold_smem &sm, uint32_t ring0, unsigned char *tab, ui
         const int Tp = max(32, nph_sub);  // phases per epoch slice
         const bool sliced = !sm.tight && 2 * Tp <= T;
         // strips as long as this sub-group's copies can be (a tile plus the widest spread,
-        // rounded to whole 16-byte units), as many as the ring holds
+        // rounded to whole 16-byte units), as many as the ring holds (at least 3); the sliced
+        // path keeps the last one for the slices' partial sums (T pairs <= one strip)
         const uint32_t stage_bytes =
             (uint32_t)((T + sm.spread + 5) & ~1) * (uint32_t)sizeof(float2);
-        rg.start(min((uint32_t)FT_NSTAGE, (uint32_t)FT_RING_BYTES / stage_bytes), stage_bytes);
+        const uint32_t ns = min((uint32_t)FT_NSTAGE, (uint32_t)FT_RING_BYTES / stage_bytes);
+        rg.start(sliced ? ns - 1 : ns, stage_bytes);
+        uint64_t *part = reinterpret_cast<uint64_t *>(raw + (ns - 1) * stage_bytes);
+        const uint32_t ring0 = smem_u32(raw);
         if (GS == 8)
-            fold_subgroup<8, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<8, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else if (GS == 4)
-            fold_subgroup<4, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<4, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else if (GS == 2)
-            fold_subgroup<2, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<2, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         else
-            fold_subgroup<1, R, KAHAN>(sm, ring0, tb, part, sliced, Tp, g0, nph_sub, ab, I,
+            fold_subgroup<1, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
                                             ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
         g0 += GS;
     }
@@ -797,11 +836,11 @@ __device__ void drain_copies(fold_smem &sm, const ring &rg) {
     for (int s = 0; s < FT_NSTAGE; ++s) mbar_wait(&sm.full[s], ((rg.par >> s) & 1u) ^ 1u);
 }
 
-__device__ __forceinline__ void fold_smem_views(unsigned char *raw, uint32_t &ring0,
-                                                unsigned char *&tab, uint64_t *&part) {
-    ring0 = smem_u32(raw);
+// Dynamic shared memory: the strip ring, the epoch table, the per-thread argmax indices.
+__device__ __forceinline__ void fold_smem_views(unsigned char *raw, unsigned char *&tab,
+                                                uint32_t *&best_at) {
     tab = raw + FT_RING_BYTES;
-    part = reinterpret_cast<uint64_t *>(tab + FT_TAB_BYTES);
+    best_at = reinterpret_cast<uint32_t *>(tab + FT_TAB_BYTES);
 }
 
 // Single light curve. Work item = (duration chunk, group); chunks outermost so that the blocks
@@ -817,10 +856,9 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
             int *__restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ fold_smem sm;
-    uint32_t ring0;
-    uint64_t *part;
     unsigned char *tab;
-    fold_smem_views(smem_raw, ring0, tab, part);
+    uint32_t *best_at;
+    fold_smem_views(smem_raw, tab, best_at);
     const int t = threadIdx.x;
     const int jc = blockIdx.x / n_groups;
     const int grp = n_groups - 1 - (int)(blockIdx.x % n_groups);
@@ -831,8 +869,8 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     block_sync();
     ring rg;
     constexpr int R = KAHAN ? FT_R / 2 : FT_R;
-    fold_group<KAHAN, R>(sm, ring0, tab, part, ab, I, ld, J, jlo, jhi, durations, mask, k0, rg,
-                         status);
+    fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, ab, I, ld, J, jlo, jhi, durations, mask, k0,
+                         rg, status);
     block_sync();
     if (sm.abort) {
         drain_copies(sm, rg);
@@ -864,10 +902,9 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
     __shared__ int s_item;
     // the queue length: n_items, or the count a device-side selection left (capped by n_items)
     if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
-    uint32_t ring0;
-    uint64_t *part;
     unsigned char *tab;
-    fold_smem_views(smem_raw, ring0, tab, part);
+    uint32_t *best_at;
+    fold_smem_views(smem_raw, tab, best_at);
     const int t = threadIdx.x;
     fold_init_barriers(sm);
     ring rg;
@@ -887,7 +924,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                            cv.I, c, p, q);
         }
         block_sync();
-        fold_group<KAHAN, R>(sm, ring0, tab, part, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
+        fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
                              durations, nullptr, 0, rg, status);
         block_sync();
         if (sm.abort) {
@@ -907,7 +944,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
 }  // namespace
 
 size_t fold_smem_bytes() {
-    return (size_t)FT_RING_BYTES + (size_t)FT_TAB_BYTES + (size_t)FT_T * sizeof(uint64_t);
+    return (size_t)FT_RING_BYTES + (size_t)FT_TAB_BYTES + (size_t)FT_G * FT_THREADS * sizeof(uint32_t);
 }
 
 cudaError_t fold_configure() {

@@ -99,13 +99,13 @@ constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear ke
 #define FT_R 4            // phases per consumer thread
 #endif
 #ifndef FT_STRIP
-#define FT_STRIP 2560     // cells per staged strip
+#define FT_STRIP 2048     // cells per staged strip at most (a tile plus the offsets' spread)
 #endif
 #ifndef FT_NSTAGE
 #define FT_NSTAGE 8       // strips in flight per block at most (as many as the ring holds)
 #endif
 #ifndef FT_RING_BYTES
-#define FT_RING_BYTES (64 * 1024)  // strip ring: FT_RING_BYTES / strip bytes stages, <= FT_NSTAGE
+#define FT_RING_BYTES (56 * 1024)  // strip ring: FT_RING_BYTES / strip bytes stages, <= FT_NSTAGE
 #endif
 #ifndef FT_MIN_BLOCKS
 #define FT_MIN_BLOCKS 2
