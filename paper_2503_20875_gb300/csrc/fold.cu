@@ -24,18 +24,19 @@
 // per cell read.
 //
 // Epoch table: per sub-group the epoch offsets are computed once in FP64 into shared memory
-// as u16 byte offsets of each period's first cell within the epoch's strip, plus the
-// smallest and largest offset of the epoch (the strip's extent). Groups whose table does not
-// fit, or whose offsets spread wider than a strip allows, are split 8 -> 4 -> 2 -> 1; a single
-// period whose table does not fit is folded straight from global memory. Periods with few
-// phases (at most T/2) fold several epochs per strip (epoch slices).
+// as byte offsets of each period's first cell within the epoch's strip (32-bit when the
+// table fits, else 16-bit), plus the smallest and largest offset of the epoch (the strip's
+// extent). Groups whose table does not fit, or whose offsets spread wider than a strip
+// allows, are split 8 -> 4 -> 2 -> 1; a single period whose table does not fit is folded
+// straight from global memory. Periods with few phases (at most T/2) fold several epochs per
+// strip (epoch slices).
 //
 // Bounded waits: every barrier wait gives up after FT_WAIT_CYCLES; the thread records
 // CETRA_ETIMEOUT in the status word and raises the block's abort flag, after which no thread
-// waits or issues a copy any more: every thread runs on through the same loops and block
-// barriers without work (no thread leaves early, so every block barrier completes), the
-// producer waits (bounded) for the copies it still has in flight, and the block exits. The
-// finalize kernel then writes NaN for every period.
+// waits or issues a copy any more: every thread runs on to the same block barriers (none
+// leaves the kernel early, so every block barrier completes), the producer waits (bounded)
+// for the copies it still has in flight, and the block exits. The finalize kernel then writes
+// NaN for every period.
 #include <cfloat>
 #include <cstdint>
 
@@ -44,11 +45,20 @@
 
 namespace {
 
-// One (A, B) cell as a packed FP32 pair (A in the low half), loaded from a 32-bit shared
-// address; sums stay packed, so no register moves are needed around the packed adds.
+// ---------------------------------------------------------------------------------------------
+// Packed (A, B) pairs and shared-memory access by 32-bit address.
+
+// One (A, B) cell as a packed FP32 pair (A in the low half); sums stay packed, so no register
+// moves are needed around the packed adds.
 __device__ __forceinline__ uint64_t lds_pair(uint32_t addr) {
     uint64_t v;
     asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ int32_t lds_s32(uint32_t addr) {
+    int32_t v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
 
@@ -96,7 +106,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // over the tile's windows in order, and decides as before.
 constexpr float kCandidate = 1.0f - 1.0f / 16384.0f;
 
-// Shared state of a fold block.
+// ---------------------------------------------------------------------------------------------
+// Shared state.
+
+// The work item a block folds: one (A, B) grid, durations [jlo, jhi), the group's mask rows.
+// Kept in shared memory so that it takes no registers in the hot loops.
+struct fold_item {
+    const float2 *ab;
+    const double *durations;
+    const uint8_t *mask;  // [K][J] or NULL; rows mask_k0 + g
+    int *status;
+    int64_t ld;
+    int I, J, jlo, jhi, mask_k0;
+};
+
 struct fold_smem {
     uint64_t full[FT_NSTAGE];        // strip landed: the producer's arrival + the copy's bytes
     uint64_t empty[FT_NSTAGE];       // strip read: one arrival per consumer thread
@@ -106,6 +129,7 @@ struct fold_smem {
     int bad, tight;                  // table votes: spread too wide for the main / sliced path
     int spread;                      // widest spread of the table's epochs (cells)
     int abort;                       // a bounded wait gave up: no more waits or copies
+    fold_item it;
 };
 
 // The strip ring as both sides see it. A sub-group uses ns strips of `bytes` each; strip s
@@ -126,46 +150,39 @@ struct ring {
     }
 };
 
-// Epoch table of a sub-group of GS periods, Es epochs:
-//   off[e][gg]  u16 byte offset of period gg's first cell o_e within strip e, whose first
-//               cell is (tmin[e] & ~1) (copies start on a 16-byte boundary);
-//   tmin[e], tmax[e]  smallest and largest o_e over the sub-group's present periods.
+// Epoch table of a sub-group of GS periods and Es epochs (shared-memory addresses):
+//   off   [Es][GS] byte offset of period g's first cell o_e(g) within strip e, whose first
+//         cell is (tmin[e] & ~1) (copies start on a 16-byte boundary): u32, or u16 (W = 2)
+//   tmin, tmax [Es]  smallest and largest o_e over the sub-group's present periods.
 struct fold_table {
-    const uint16_t *off;
-    const int32_t *tmin, *tmax;
+    uint32_t off, tmin, tmax;
     int Es;
+    __device__ __forceinline__ int lo(int e) const { return lds_s32(tmin + 4u * (uint32_t)e); }
+    __device__ __forceinline__ int hi(int e) const { return lds_s32(tmax + 4u * (uint32_t)e); }
 };
 
-__host__ __device__ constexpr int64_t table_off_bytes(int64_t Es, int GS) {
-    return ((Es * GS * 2) + 15) & ~(int64_t)15;
+__host__ __device__ constexpr int64_t table_off_bytes(int64_t Es, int GS, int W) {
+    return ((Es * GS * W) + 15) & ~(int64_t)15;
 }
-__host__ __device__ constexpr int64_t table_bytes(int64_t Es, int GS) {
-    return table_off_bytes(Es, GS) + 8 * Es;
-}
-
-__device__ __forceinline__ fold_table table_view(const unsigned char *raw, int Es, int GS) {
-    fold_table t;
-    t.off = reinterpret_cast<const uint16_t *>(raw);
-    t.tmin = reinterpret_cast<const int32_t *>(raw + table_off_bytes(Es, GS));
-    t.tmax = t.tmin + Es;
-    t.Es = Es;
-    return t;
+__host__ __device__ constexpr int64_t table_bytes(int64_t Es, int GS, int W) {
+    return table_off_bytes(Es, GS, W) + 8 * Es;
 }
 
-// The byte offsets of one epoch's GS periods, two per 32-bit word.
-template <int GS>
-struct packed_offsets {
-    static constexpr int W = (GS + 1) / 2;
-    uint32_t w[W];
-    __device__ __forceinline__ void load(const uint16_t *row) {
-        const uint32_t a = smem_u32(row);
-        if constexpr (GS == 8) {
-            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-                         : "r"(a));
-        } else if constexpr (GS == 4) {
+// The byte offsets of one epoch's GS periods: W = 4 bytes each, or W = 2 (two per word).
+template <int GS, int W>
+struct epoch_offsets {
+    static constexpr int N = W == 4 ? GS : (GS + 1) / 2;
+    uint32_t w[N];
+    __device__ __forceinline__ void load(uint32_t a) {
+        if constexpr (N >= 4) {
+#pragma unroll
+            for (int k = 0; k < N; k += 4)
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(w[k]), "=r"(w[k + 1]), "=r"(w[k + 2]), "=r"(w[k + 3])
+                             : "r"(a + 4u * k));
+        } else if constexpr (N == 2) {
             asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a));
-        } else if constexpr (GS == 2) {
+        } else if constexpr (W == 4 || GS == 2) {
             asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w[0]) : "r"(a));
         } else {
             uint16_t h;
@@ -174,53 +191,74 @@ struct packed_offsets {
         }
     }
     __device__ __forceinline__ uint32_t operator[](int g) const {
+        if constexpr (W == 4) return w[g];
         return (g & 1) ? (w[g >> 1] >> 16) : (w[g >> 1] & 0xFFFFu);
     }
 };
 
-// Bit gg set when period g0 + gg is folded at duration D: it has epochs, D < P (Sec. 2.3)
-// and the caller's mask allows the pair (mask rows mask_k0 + g).
+// Bit gg set when period g0 + gg is folded at duration j: it has epochs, D_j < P (Sec. 2.3)
+// and the caller's mask allows the pair.
 template <int GS>
-__device__ __forceinline__ unsigned period_use(const fold_smem &sm, int g0, double D, int j, int J,
-                                               const uint8_t *__restrict__ mask, int mask_k0) {
+__device__ __forceinline__ unsigned period_use(const fold_smem &sm, int g0, int j) {
+    const double D = sm.it.durations[j];
+    const uint8_t *mask = sm.it.mask;
     unsigned use = 0u;
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
         const int g = g0 + gg;
-        if (sm.E[g] > 0 && D < sm.P[g] && (!mask || mask[(int64_t)(mask_k0 + g) * J + j]))
+        if (sm.E[g] > 0 && D < sm.P[g] &&
+            (!mask || mask[(int64_t)(sm.it.mask_k0 + g) * sm.it.J + j]))
             use |= 1u << gg;
     }
     return use;
 }
 
-// Bounded wait of the fold, called by whole warps; the result is the same for every lane
+__device__ __forceinline__ void record_timeout(fold_smem &sm) {
+    if (!*(volatile int *)&sm.abort) {
+        *(volatile int *)&sm.abort = 1;
+        atomicExch(sm.it.status, CETRA_ETIMEOUT);
+    }
+}
+
+// Consumers' bounded wait, called by whole warps; the result is the same for every lane
 // (false if any lane's wait gave up, or if the phase is not complete and the block has
-// aborted). A wait that gives up records the time-out and aborts the block; the finalize
-// kernel then writes NaN for every period.
-__device__ __noinline__ bool fold_wait_slow(fold_smem &sm, uint64_t *bar, uint32_t parity,
-                                            int *status) {
+// aborted). A wait that gives up records the time-out and aborts the block.
+__device__ __noinline__ bool fold_wait_slow(fold_smem &sm, uint64_t *bar, uint32_t parity) {
     bool ok = true;
     if (!mbar_test(bar, parity)) {
         ok = !*(volatile int *)&sm.abort && mbar_wait(bar, parity);
-        if (!ok && !*(volatile int *)&sm.abort) {
-            *(volatile int *)&sm.abort = 1;
-            atomicExch(status, CETRA_ETIMEOUT);
-        }
+        if (!ok) record_timeout(sm);
     }
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
-__device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t parity,
-                                          int *status) {
+__device__ __forceinline__ bool fold_wait(fold_smem &sm, uint64_t *bar, uint32_t parity) {
     if (__all_sync(0xFFFFFFFFu, mbar_test(bar, parity))) return true;  // the phase is complete
-    return fold_wait_slow(sm, bar, parity, status);
+    return fold_wait_slow(sm, bar, parity);
+}
+
+// The producer's bounded wait, by its one issuing lane, which sleeps in the barrier's
+// potentially blocking test instead of spinning.
+__device__ __forceinline__ bool producer_wait(fold_smem &sm, uint64_t *bar, uint32_t parity) {
+    if (mbar_wait(bar, parity)) return true;
+    record_timeout(sm);
+    return false;
+}
+
+// One bulk copy of cells [a, a + len) of grid row j into the ring's current strip.
+__device__ __forceinline__ void issue_copy(fold_smem &sm, uint32_t ring0, const ring &rg, int j,
+                                           int a, int len) {
+    const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
+    const float2 *src = sm.it.ab + (int64_t)j * sm.it.ld + a;
+    fence_proxy_async();
+    mbar_expect_tx(&sm.full[rg.stage], bytes);
+    bulk_load_s(ring0 + rg.stage * rg.bytes, src, bytes, &sm.full[rg.stage]);
 }
 
 // Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
-// slot's best key in shared memory.
-// The flat index of each thread's best window of period slot g is kept in shared memory,
-// best_at[g * FT_THREADS + c]: it is written only when a maximum changes, so it need not take
-// registers in the hot loop.
+// slot's best key in shared memory. The flat index of a thread's best window of slot g is
+// kept in shared memory, best_at[g * FT_THREADS + c]: it is written only when a maximum
+// changes, so it takes no register in the hot loop.
 template <int GS>
 __device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float *best_lr2,
                                              const uint32_t *best_at) {
@@ -256,54 +294,44 @@ __device__ __forceinline__ void take_max(float x, float y, uint32_t at, float &b
 // Live epochs of a tile starting at phase i0: e < Es with tmin[e] < I - i0 (tmin is
 // nondecreasing in e, so they are a prefix); nE only shrinks as i0 grows.
 __device__ __forceinline__ int live_epochs(const fold_table &tb, int nE, int I, int i0) {
-    while (nE > 0 && tb.tmin[nE - 1] >= I - i0) --nE;
+    while (nE > 0 && tb.lo(nE - 1) >= I - i0) --nE;
     return nE;
 }
 
+// Run by the producer warp's first lane alone.
 template <int GS, int R>
 __device__ void produce_main(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
-                             int nph_sub, const float2 *__restrict__ ab, int I, int64_t ld, int J,
-                             int jlo, int jhi, const double *__restrict__ durations,
-                             const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                             int *__restrict__ status) {
+                             int nph_sub, ring &rg) {
     constexpr int T = FT_THREADS * R;
-    const bool leader = (threadIdx.x & 31) == 0;
-    for (int j = jlo; j < jhi; ++j) {
-        if (!period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0)) continue;
-        const float2 *row = ab + (int64_t)j * ld;
+    const int I = sm.it.I;
+    for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
+        if (!period_use<GS>(sm, g0, j)) continue;
         int nE = tb.Es;
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
             nE = live_epochs(tb, nE, I, i0);
             for (int e = 0; e < nE; ++e) {
-                if (!fold_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u, status)) return;
-                if (leader) {
-                    const int a = i0 + (tb.tmin[e] & ~1);
-                    const int len = ((i0 + tb.tmax[e] + T - a) + 1) & ~1;
-                    const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
-                    fence_proxy_async();
-                    mbar_expect_tx(&sm.full[rg.stage], bytes);
-                    bulk_load_s(ring0 + rg.stage * rg.bytes, row + a, bytes, &sm.full[rg.stage]);
-                }
-                __syncwarp();
+                if (!producer_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u)) return;
+                const int a = i0 + (tb.lo(e) & ~1);
+                issue_copy(sm, ring0, rg, j, a, ((i0 + tb.hi(e) + T - a) + 1) & ~1);
                 rg.next();
             }
         }
     }
 }
 
-// Epochs 2 .. nE-1 of a tile (epochs 0 and 1 initialised acc): ALL = every period of the
+// Epochs 2 .. nE-1 of a tile (epochs 0 and 1 started the sums): ALL = every period of the
 // sub-group is folded at this duration (no per-period test in the loop).
-template <int GS, int R, bool KAHAN, bool ALL>
+template <int GS, int R, int W, bool KAHAN, bool ALL>
 __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &tb, int nE,
                                                unsigned use, uint32_t mine, uint64_t (&acc)[GS][R],
                                                uint64_t (&cmp)[KAHAN ? GS : 1][KAHAN ? R : 1],
-                                               ring &rg, int *__restrict__ status) {
+                                               ring &rg) {
     constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
     for (int e = 2; e < nE; ++e) {
-        if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return false;
+        if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
         const uint32_t a = mine + rg.stage * rg.bytes;
-        packed_offsets<GS> off;
-        off.load(tb.off + e * GS);
+        epoch_offsets<GS, W> off;
+        off.load(tb.off + (uint32_t)(e * GS * W));
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg) {
             if (!ALL && !((use >> gg) & 1u)) continue;
@@ -325,12 +353,9 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
     return true;
 }
 
-template <int GS, int R, bool KAHAN>
+template <int GS, int R, int W, bool KAHAN>
 __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
-                             const fold_table &tb, int g0, int nph_sub, int I, int J, int jlo,
-                             int jhi, const double *__restrict__ durations,
-                             const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                             int *__restrict__ status) {
+                             const fold_table &tb, int g0, int nph_sub, ring &rg) {
     constexpr int T = FT_THREADS * R;
     constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
     const int c = threadIdx.x;
@@ -341,24 +366,20 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
         best_lr2[gg] = -1.0f;
         best_at[gg * FT_THREADS + c] = 0u;
     }
-    for (int j = jlo; j < jhi; ++j) {
-        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+    for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, j);
         if (!use) continue;
         const bool all_used = use == (1u << GS) - 1u;
-        int nmin = I;  // phases every used period has
-#pragma unroll
-        for (int gg = 0; gg < GS; ++gg)
-            if ((use >> gg) & 1u) nmin = min(nmin, sm.nph[g0 + gg]);
         int nE = tb.Es;
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
-            nE = live_epochs(tb, nE, I, i0);
+            nE = live_epochs(tb, nE, sm.it.I, i0);
             uint64_t acc[GS][R];
             uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
             // Epoch 0: every period's cell is its phase cell (o_0 = 0), one load for all.
             // Epoch 1 then starts each sum as (epoch-0 cell + epoch-1 cell). (A wait that gave
             // up ends the path at once: the main path has no block barrier, so every thread
             // still meets the caller's next one.)
-            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return;
+            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return;
             uint64_t v0[R];
             {
                 const uint32_t a = mine + rg.stage * rg.bytes;
@@ -380,10 +401,10 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
                 }
             }
             if (nE >= 2) {
-                if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) return;
+                if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return;
                 const uint32_t a = mine + rg.stage * rg.bytes;
-                packed_offsets<GS> off;
-                off.load(tb.off + GS);
+                epoch_offsets<GS, W> off;
+                off.load(tb.off + (uint32_t)(GS * W));
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     const uint32_t ag = a + off[gg];
@@ -402,16 +423,18 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
                 rg.next();
             }
             const bool ok =
-                all_used
-                    ? consume_epochs<GS, R, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg, status)
-                    : consume_epochs<GS, R, KAHAN, false>(sm, tb, nE, use, mine, acc, cmp, rg, status);
+                all_used ? consume_epochs<GS, R, W, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg)
+                         : consume_epochs<GS, R, W, KAHAN, false>(sm, tb, nE, use, mine, acc, cmp, rg);
             if (!ok) return;
             // 2 LR = SA^2 / SB per (period, phase); the running maximum keeps the first
             // (smallest j, then smallest i) of equal values. Whole tiles first run the
             // candidate test over all their windows.
-            const bool whole = i0 + T <= nmin;
-            bool any = !whole;
-            if (whole) {
+            int nmin = nph_sub;  // phases every used period has
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg)
+                if ((use >> gg) & 1u) nmin = min(nmin, sm.nph[g0 + gg]);
+            bool any = i0 + T > nmin;
+            if (!any) {
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     if (!all_used && !((use >> gg) & 1u)) continue;
@@ -427,6 +450,7 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
                 }
             }
             if (any) {
+                const uint32_t jI = (uint32_t)j * (uint32_t)sm.it.I;
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     if (!((use >> gg) & 1u)) continue;
@@ -439,7 +463,7 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
                         float x, y;
                         split_pair(v, x, y);
                         if (i < nph)
-                            take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)i, best_lr2[gg],
+                            take_max(x, y, jI + (uint32_t)i, best_lr2[gg],
                                      &best_at[gg * FT_THREADS + c]);
                     }
                 }
@@ -460,36 +484,28 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
 // spread <= FT_STRIP - T - 8 for this path.)
 
 __device__ __forceinline__ bool live_epoch(const fold_table &tb, int e, int I) {
-    return e < tb.Es && tb.tmin[e] < I;
+    return e < tb.Es && tb.lo(e) < I;
 }
 
 template <int GS, int R>
 __device__ void produce_sliced(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
-                               int Tp, const float2 *__restrict__ ab, int I, int64_t ld, int J,
-                               int jlo, int jhi, const double *__restrict__ durations,
-                               const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                               int *__restrict__ status) {
+                               int Tp, ring &rg) {
     constexpr int T = FT_THREADS * R;
     const int H = T / Tp;
+    const int I = sm.it.I;
     const bool leader = (threadIdx.x & 31) == 0;
-    for (int j = jlo; j < jhi; ++j) {
-        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+    for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, j);
         if (!use) continue;
-        const float2 *row = ab + (int64_t)j * ld;
         for (int s = 0; live_epoch(tb, s * H, I); ++s) {
             // (after an abort this only keeps the loop, and the barriers below, in step)
-            const bool ok = fold_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u, status);
-            if (leader && ok) {
+            if (leader && producer_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u)) {
                 const int e0 = s * H;
-                const int a = tb.tmin[e0] & ~1;
+                const int a = tb.lo(e0) & ~1;
                 int end = 0;
                 for (int h = 0; h < H; ++h)
-                    if (live_epoch(tb, e0 + h, I)) end = max(end, tb.tmax[e0 + h] + Tp);
-                const int len = ((end - a) + 1) & ~1;
-                const uint32_t bytes = (uint32_t)len * (uint32_t)sizeof(float2);
-                fence_proxy_async();
-                mbar_expect_tx(&sm.full[rg.stage], bytes);
-                bulk_load_s(ring0 + rg.stage * rg.bytes, row + a, bytes, &sm.full[rg.stage]);
+                    if (live_epoch(tb, e0 + h, I)) end = max(end, tb.hi(e0 + h) + Tp);
+                issue_copy(sm, ring0, rg, j, a, ((end - a) + 1) & ~1);
             }
             __syncwarp();
             rg.next();
@@ -503,15 +519,13 @@ __device__ void produce_sliced(fold_smem &sm, uint32_t ring0, const fold_table &
     }
 }
 
-template <int GS, int R, bool KAHAN>
+template <int GS, int R, int W, bool KAHAN>
 __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, uint32_t *best_at,
-                               const fold_table &tb, int g0, int Tp, int I, int J, int jlo,
-                               int jhi, const double *__restrict__ durations,
-                               const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                               int *__restrict__ status) {
+                               const fold_table &tb, int g0, int Tp, ring &rg) {
     constexpr int T = FT_THREADS * R;
     const int H = T / Tp;
     const int c = threadIdx.x;
+    const int I = sm.it.I;
     int slice[R], phase[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -525,8 +539,8 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
         best_lr2[gg] = -1.0f;
         best_at[gg * FT_THREADS + c] = 0u;
     }
-    for (int j = jlo; j < jhi; ++j) {
-        const unsigned use = period_use<GS>(sm, g0, durations[j], j, J, mask, mask_k0);
+    for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
+        const unsigned use = period_use<GS>(sm, g0, j);
         if (!use) continue;
         const bool all_used = use == (1u << GS) - 1u;
         uint64_t acc[GS][R];
@@ -543,11 +557,11 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
         }
         for (int s = 0; live_epoch(tb, s * H, I); ++s) {
             // after an abort the loop runs on without work, to keep the barriers below in step
-            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity(), status)) {
+            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) {
                 rg.next();
                 continue;
             }
-            const int a_s = tb.tmin[s * H] & ~1;
+            const int a_s = tb.lo(s * H) & ~1;
             const uint32_t stage = ring0 + rg.stage * rg.bytes;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -555,9 +569,9 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
                 const int e = s * H + slice[r];
                 if (!live_epoch(tb, e, I)) continue;
                 const uint32_t lb =
-                    stage + (uint32_t)(phase[r] + (tb.tmin[e] & ~1) - a_s) * (uint32_t)sizeof(float2);
-                packed_offsets<GS> off;
-                off.load(tb.off + e * GS);
+                    stage + (uint32_t)(phase[r] + (tb.lo(e) & ~1) - a_s) * (uint32_t)sizeof(float2);
+                epoch_offsets<GS, W> off;
+                off.load(tb.off + (uint32_t)(e * GS * W));
 #pragma unroll
                 for (int gg = 0; gg < GS; ++gg) {
                     if (!all_used && !((use >> gg) & 1u)) continue;
@@ -600,17 +614,14 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
 
 // ---------------------------------------------------------------------------------------------
 // One period whose epoch table does not fit: straight from global memory (consumers only).
-__device__ void fold_direct(fold_smem &sm, int g, int mask_row, const float2 *__restrict__ ab,
-                            int I, int64_t ld, int J, int jlo, int jhi,
-                            const double *__restrict__ durations,
-                            const uint8_t *__restrict__ mask) {
+__device__ void fold_direct(fold_smem &sm, int g) {
     const int c = threadIdx.x;
     const double Ps = sm.Ps[g];
+    const int I = sm.it.I;
     unsigned long long best = 0ull;
-    for (int j = jlo; j < jhi; ++j) {
-        if (!(durations[j] < sm.P[g])) continue;
-        if (mask && !mask[(int64_t)mask_row * J + j]) continue;
-        const float2 *row = ab + (int64_t)j * ld;
+    for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
+        if (!period_use<1>(sm, g, j)) continue;
+        const float2 *row = sm.it.ab + (int64_t)j * sm.it.ld;
         for (int i = c; i < sm.nph[g]; i += FT_THREADS) {
             float2 acc = make_float2(0.f, 0.f);
             for (int64_t e = 0;; ++e) {
@@ -660,14 +671,15 @@ __device__ __forceinline__ void fold_slot_meta(fold_smem &sm, int t, bool presen
     sm.best[t] = 0ull;
 }
 
-// Build the epoch table of sub-group [g0, g0 + GS) (all threads). Sets sm.bad when some
-// epoch's spread leaves no room for a tile in a strip, sm.tight when it leaves less than the
-// sliced path's margin. Offsets beyond the t0 grid are kept (their cells are the zero padding
-// after each grid row), so a strip never needs clipping.
-template <int GS>
+// Build the epoch table of sub-group [g0, g0 + GS) (all threads), offsets W bytes wide. Sets
+// sm.bad when some epoch's spread leaves no room for a tile in a strip, sm.tight when it
+// leaves less than the sliced path's margin, sm.spread to the widest spread. Offsets beyond
+// the t0 grid are kept (their cells are the zero padding after each grid row), so a strip
+// never needs clipping.
+template <int GS, int W>
 __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, int T) {
-    uint16_t *off = reinterpret_cast<uint16_t *>(raw);
-    int32_t *tmin = reinterpret_cast<int32_t *>(raw + table_off_bytes(Es, GS));
+    unsigned char *off = raw;
+    int32_t *tmin = reinterpret_cast<int32_t *>(raw + table_off_bytes(Es, GS, W));
     int32_t *tmax = tmin + Es;
     bool bad = false, tight = false;
     int64_t widest = 0;
@@ -693,8 +705,12 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
         widest = spread > widest ? spread : widest;
 #pragma unroll
         for (int gg = 0; gg < GS; ++gg) {
-            const int64_t d = o[gg] >= 0 ? (o[gg] - base) * (int64_t)sizeof(float2) : 0;
-            off[e * GS + gg] = (uint16_t)(d >= 0 && d < 65536 ? d : 0);
+            int64_t d = o[gg] >= 0 ? (o[gg] - base) * (int64_t)sizeof(float2) : 0;
+            d = d >= 0 && d < 65536 ? d : 0;
+            if constexpr (W == 4)
+                reinterpret_cast<uint32_t *>(off)[e * GS + gg] = (uint32_t)d;
+            else
+                reinterpret_cast<uint16_t *>(off)[e * GS + gg] = (uint16_t)d;
         }
         tmin[e] = (int32_t)mn;
         tmax[e] = (int32_t)mx;
@@ -704,51 +720,64 @@ __device__ void build_table(fold_smem &sm, unsigned char *raw, int g0, int Es, i
     if (!bad && widest > 0) atomicMax(&sm.spread, (int)widest);
 }
 
-template <int GS, int R, bool KAHAN>
+template <int GS>
+__device__ __forceinline__ void build_table_w(fold_smem &sm, unsigned char *raw, int g0, int Es,
+                                              int T, int W) {
+    if (W == 4)
+        build_table<GS, 4>(sm, raw, g0, Es, T);
+    else
+        build_table<GS, 2>(sm, raw, g0, Es, T);
+}
+
+template <int GS, int R, int W, bool KAHAN>
 __device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &tb, uint64_t *part,
                               uint32_t *best_at, bool sliced, int Tp, int g0, int nph_sub,
-                              const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
-                              int jhi, const double *__restrict__ durations,
-                              const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                              int *__restrict__ status) {
+                              ring &rg) {
     const bool producer = threadIdx.x >= FT_THREADS;
     if (sliced) {
         if (producer)
-            produce_sliced<GS, R>(sm, ring0, tb, g0, Tp, ab, I, ld, J, jlo, jhi, durations, mask,
-                                  mask_k0, rg, status);
+            produce_sliced<GS, R>(sm, ring0, tb, g0, Tp, rg);
         else
-            consume_sliced<GS, R, KAHAN>(sm, ring0, part, best_at, tb, g0, Tp, I, J, jlo, jhi,
-                                         durations, mask, mask_k0, rg, status);
+            consume_sliced<GS, R, W, KAHAN>(sm, ring0, part, best_at, tb, g0, Tp, rg);
     } else if (producer) {
-        produce_main<GS, R>(sm, ring0, tb, g0, nph_sub, ab, I, ld, J, jlo, jhi, durations, mask,
-                            mask_k0, rg, status);
+        // the main path has no block barrier: the producer's first lane runs it alone
+        if ((threadIdx.x & 31) == 0) produce_main<GS, R>(sm, ring0, tb, g0, nph_sub, rg);
+        __syncwarp();
     } else {
-        consume_main<GS, R, KAHAN>(sm, ring0, best_at, tb, g0, nph_sub, I, J, jlo, jhi, durations,
-                                   mask, mask_k0, rg, status);
+        consume_main<GS, R, W, KAHAN>(sm, ring0, best_at, tb, g0, nph_sub, rg);
     }
 }
 
-// Fold the group whose slot metadata is in `sm` over durations [jlo, jhi) of one (A, B)
-// grid: every sub-group (8 -> 4 -> 2 -> 1 periods, as the table allows) in turn; slot g's
-// best key ends in sm.best[g]. Mask rows are (mask_k0 + g). A wait that gave up leaves
-// sm.abort set.
+template <int GS, int R, bool KAHAN>
+__device__ __forceinline__ void fold_subgroup_w(fold_smem &sm, uint32_t ring0,
+                                                const fold_table &tb, uint64_t *part,
+                                                uint32_t *best_at, bool sliced, int Tp, int g0,
+                                                int nph_sub, ring &rg, int W) {
+    if (W == 4)
+        fold_subgroup<GS, R, 4, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg);
+    else
+        fold_subgroup<GS, R, 2, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg);
+}
+
+// Fold the group whose slot metadata and work item are in `sm` (all threads): every sub-group
+// (8 -> 4 -> 2 -> 1 periods, as the table allows) in turn; slot g's best key ends in
+// sm.best[g]. A wait that gave up leaves sm.abort set.
 template <bool KAHAN, int R>
-__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab, uint32_t *best_at,
-                           const float2 *__restrict__ ab, int I, int64_t ld, int J, int jlo,
-                           int jhi, const double *__restrict__ durations,
-                           const uint8_t *__restrict__ mask, int mask_k0, ring &rg,
-                           int *__restrict__ status) {
+__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab,
+                           uint32_t *best_at, ring &rg) {
     constexpr int T = FT_THREADS * R;
     for (int g0 = 0; g0 < FT_G;) {
         int GS = FT_G;
         while (g0 % GS) GS >>= 1;
-        int Es = 0;
+        int Es = 0, W = 4;
         bool table_ok = false;
         for (;;) {
             Es = 0;
             for (int g = g0; g < g0 + GS; ++g) Es = max(Es, sm.E[g]);
             if (Es == 0) break;  // no period of the sub-group has a phase
-            if (table_bytes(Es, GS) > FT_TAB_BYTES) {
+            // 32-bit offsets when they fit, else 16-bit
+            W = table_bytes(Es, GS, 4) <= FT_TAB_BYTES ? 4 : 2;
+            if (table_bytes(Es, GS, W) > FT_TAB_BYTES) {
                 if (GS > 1) {
                     GS >>= 1;
                     continue;
@@ -759,13 +788,13 @@ __device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab
             if (threadIdx.x == 0) sm.bad = sm.tight = sm.spread = 0;
             block_sync();
             if (GS == 8)
-                build_table<8>(sm, tab, g0, Es, T);
+                build_table_w<8>(sm, tab, g0, Es, T, W);
             else if (GS == 4)
-                build_table<4>(sm, tab, g0, Es, T);
+                build_table_w<4>(sm, tab, g0, Es, T, W);
             else if (GS == 2)
-                build_table<2>(sm, tab, g0, Es, T);
+                build_table_w<2>(sm, tab, g0, Es, T, W);
             else
-                build_table<1>(sm, tab, g0, Es, T);
+                build_table_w<1>(sm, tab, g0, Es, T, W);
             block_sync();
             if (sm.bad && GS > 1) {
                 GS >>= 1;
@@ -782,12 +811,15 @@ __device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab
         }
         if (!table_ok) {
             // GS == 1 here
-            if (threadIdx.x < FT_THREADS)
-                fold_direct(sm, g0, mask_k0 + g0, ab, I, ld, J, jlo, jhi, durations, mask);
+            if (threadIdx.x < FT_THREADS) fold_direct(sm, g0);
             g0 += GS;
             continue;
         }
-        const fold_table tb = table_view(tab, Es, GS);
+        fold_table tb;
+        tb.off = smem_u32(tab);
+        tb.tmin = tb.off + (uint32_t)table_off_bytes(Es, GS, W);
+        tb.tmax = tb.tmin + 4u * (uint32_t)Es;
+        tb.Es = Es;
         const int Tp = max(32, nph_sub);  // phases per epoch slice
         const bool sliced = !sm.tight && 2 * Tp <= T;
         // strips as long as this sub-group's copies can be (a tile plus the widest spread,
@@ -800,17 +832,13 @@ __device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab
         uint64_t *part = reinterpret_cast<uint64_t *>(raw + (ns - 1) * stage_bytes);
         const uint32_t ring0 = smem_u32(raw);
         if (GS == 8)
-            fold_subgroup<8, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
-                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+            fold_subgroup_w<8, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
         else if (GS == 4)
-            fold_subgroup<4, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
-                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+            fold_subgroup_w<4, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
         else if (GS == 2)
-            fold_subgroup<2, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
-                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+            fold_subgroup_w<2, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
         else
-            fold_subgroup<1, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, ab, I,
-                                            ld, J, jlo, jhi, durations, mask, mask_k0, rg, status);
+            fold_subgroup_w<1, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
         g0 += GS;
     }
 }
@@ -828,11 +856,11 @@ __device__ __forceinline__ void fold_init_barriers(fold_smem &sm) {
     }
 }
 
-// A block that aborted: the producer waits (bounded) for the last fill of every strip to
-// land, so that no copy lands in shared memory after the block exits. (A strip never filled
-// has parity bit 0: its wait on phase parity 1 passes at once.)
+// A block that aborted: the producer's first lane waits (bounded) for the last fill of every
+// strip to land, so that no copy lands in shared memory after the block exits. (A strip
+// never filled has parity bit 0: its wait on phase parity 1 passes at once.)
 __device__ void drain_copies(fold_smem &sm, const ring &rg) {
-    if (threadIdx.x < FT_THREADS) return;
+    if (threadIdx.x != FT_THREADS) return;  // the producer's issuing lane holds the ring state
     for (int s = 0; s < FT_NSTAGE; ++s) mbar_wait(&sm.full[s], ((rg.par >> s) & 1u) ^ 1u);
 }
 
@@ -862,15 +890,25 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     const int t = threadIdx.x;
     const int jc = blockIdx.x / n_groups;
     const int grp = n_groups - 1 - (int)(blockIdx.x % n_groups);
-    const int jlo = jc * jchunk, jhi = min(J, jlo + jchunk);
     const int k0 = grp * FT_G;
     fold_init_barriers(sm);
+    if (t == 0) {
+        sm.it.ab = ab;
+        sm.it.durations = durations;
+        sm.it.mask = mask;
+        sm.it.status = status;
+        sm.it.ld = ld;
+        sm.it.I = I;
+        sm.it.J = J;
+        sm.it.jlo = jc * jchunk;
+        sm.it.jhi = min(J, sm.it.jlo + jchunk);
+        sm.it.mask_k0 = k0;
+    }
     if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
     block_sync();
     ring rg;
     constexpr int R = KAHAN ? FT_R / 2 : FT_R;
-    fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, ab, I, ld, J, jlo, jhi, durations, mask, k0,
-                         rg, status);
+    fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, rg);
     block_sync();
     if (sm.abort) {
         drain_copies(sm, rg);
@@ -918,14 +956,25 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
         const int cidx = csr_find(group_off, n_curves, item);
         const batch_curve cv = curves[cidx];
         const int k0 = (int)(item - group_off[cidx]) * FT_G;
+        if (t == 0) {
+            sm.it.ab = ab + cv.ab_off;
+            sm.it.durations = durations;
+            sm.it.mask = nullptr;
+            sm.it.status = status;
+            sm.it.ld = cv.ld;
+            sm.it.I = cv.I;
+            sm.it.J = J;
+            sm.it.jlo = 0;
+            sm.it.jhi = J;
+            sm.it.mask_k0 = 0;
+        }
         if (t < FT_G) {
             const bool present = k0 + t < cv.n_periods;
             fold_slot_meta(sm, t, present, present ? batch_period(cv.pmin, cv.ratio, k0 + t) : 0.0,
                            cv.I, c, p, q);
         }
         block_sync();
-        fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, ab + cv.ab_off, cv.I, cv.ld, J, 0, J,
-                             durations, nullptr, 0, rg, status);
+        fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, rg);
         block_sync();
         if (sm.abort) {
             drain_copies(sm, rg);
