@@ -56,6 +56,18 @@ __device__ __forceinline__ uint64_t lds_pair(uint32_t addr) {
     return v;
 }
 
+// v[k] = the pair at addr + k FT_THREADS * 8 (k < R): the rows of R phases a thread owns in a
+// strip, with the row step as an immediate offset of each load.
+template <int K, int R>
+__device__ __forceinline__ void lds_rows(uint64_t (&v)[R], uint32_t addr) {
+    if constexpr (K < R) {
+        asm volatile("ld.shared.b64 %0, [%1+%2];"
+                     : "=l"(v[K])
+                     : "r"(addr), "n"(K * FT_THREADS * (int)sizeof(float2)));
+        lds_rows<K + 1, R>(v, addr);
+    }
+}
+
 __device__ __forceinline__ int32_t lds_s32(uint32_t addr) {
     int32_t v;
     asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
@@ -100,10 +112,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Candidate test of the epilogue: the exact comparison of a window's 2 LR = x^2 / y with the
 // running best b is x * __fdividef(x, y) > b, whose left side has a relative error below
-// 2^-21. With h = b (1 - 2^-14) rounded once, x^2 > h y (each product rounded once) holds
-// whenever the exact comparison does (for b <= 0 trivially, for b > 0 by the margin), so a
-// tile in which no window passes it has no new maximum; otherwise the exact comparison runs
-// over the tile's windows in order, and decides as before.
+// 2^-21. With h = b (1 - 2^-14) and q = h y (each rounded once), fma(x, x, -q) > 0 (the exact
+// x^2 - q, rounded) holds whenever the exact comparison does (for b <= 0 trivially, for b > 0
+// by the margin), so a tile whose largest fma(x, x, -q) is not positive has no new maximum;
+// otherwise the exact comparison runs over the tile's windows in order, and decides as before.
 constexpr float kCandidate = 1.0f - 1.0f / 16384.0f;
 
 // ---------------------------------------------------------------------------------------------
@@ -255,19 +267,33 @@ __device__ __forceinline__ void issue_copy(fold_smem &sm, uint32_t ring0, const 
     bulk_load_s(ring0 + rg.stage * rg.bytes, src, bytes, &sm.full[rg.stage]);
 }
 
-// Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
-// slot's best key in shared memory. The flat index of a thread's best window of slot g is
-// kept in shared memory, best_at[g * FT_THREADS + c]: it is written only when a maximum
-// changes, so it takes no register in the hot loop.
+// A consumer thread's running maximum of each period of the sub-group, in shared memory: slot
+// gg of thread c at [gg * FT_THREADS + c], the largest 2 LR so far and the flat index of its
+// window. They are read once per tile and written only when a maximum changes, so they take
+// no registers in the hot loop.
+struct best_slots {
+    float *lr2;
+    uint32_t *at;
+};
+
 template <int GS>
-__device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float *best_lr2,
-                                             const uint32_t *best_at) {
+__device__ __forceinline__ void init_best(best_slots bs) {
+#pragma unroll
+    for (int gg = 0; gg < GS; ++gg) {
+        bs.lr2[gg * FT_THREADS + threadIdx.x] = -1.0f;
+        bs.at[gg * FT_THREADS + threadIdx.x] = 0u;
+    }
+}
+
+// Per-thread best of each period (the largest 2 LR, first in (j, i) order on ties) -> the
+// slot's best key in shared memory.
+template <int GS>
+__device__ __forceinline__ void publish_best(fold_smem &sm, int g0, best_slots bs) {
     const int c = threadIdx.x;
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
-        unsigned long long key =
-            best_lr2[gg] >= 0.0f ? make_key(0.5f * best_lr2[gg], best_at[gg * FT_THREADS + c])
-                                 : 0ull;
+        const float b = bs.lr2[gg * FT_THREADS + c];
+        unsigned long long key = b >= 0.0f ? make_key(0.5f * b, bs.at[gg * FT_THREADS + c]) : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, key, o);
@@ -279,12 +305,12 @@ __device__ __forceinline__ void publish_best(fold_smem &sm, int g0, const float 
 
 // Exact running maximum over one window sum (x, y) = (sum A, sum B) at flat index at:
 // 2 LR = x * (x / y); a null sum gives NaN, never a maximum; the first of equal values stays.
-__device__ __forceinline__ void take_max(float x, float y, uint32_t at, float &best_lr2,
-                                         uint32_t *best_at) {
+__device__ __forceinline__ void take_max(float x, float y, uint32_t at, best_slots bs, int gg) {
+    const int k = gg * FT_THREADS + threadIdx.x;
     const float lr2 = x * __fdividef(x, y);
-    if (lr2 > best_lr2) {
-        best_lr2 = lr2;
-        *best_at = at;
+    if (lr2 > bs.lr2[k]) {
+        bs.lr2[k] = lr2;
+        bs.at[k] = at;
     }
 }
 
@@ -326,7 +352,6 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
                                                unsigned use, uint32_t mine, uint64_t (&acc)[GS][R],
                                                uint64_t (&cmp)[KAHAN ? GS : 1][KAHAN ? R : 1],
                                                ring &rg) {
-    constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
     for (int e = 2; e < nE; ++e) {
         if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
         const uint32_t a = mine + rg.stage * rg.bytes;
@@ -337,8 +362,7 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
             if (!ALL && !((use >> gg) & 1u)) continue;
             const uint32_t ag = a + off[gg];
             uint64_t v[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = lds_pair(ag + r * kRowStep);
+            lds_rows<0, R>(v, ag);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if constexpr (KAHAN)
@@ -353,124 +377,154 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
     return true;
 }
 
-template <int GS, int R, int W, bool KAHAN>
-__device__ void consume_main(fold_smem &sm, uint32_t ring0, uint32_t *best_at,
-                             const fold_table &tb, int g0, int nph_sub, ring &rg) {
+// One tile of the main path: epochs 0 .. nE-1 into acc, then the running maxima. SHORT: the
+// tile has at most 3 live epochs and runs as straight-line code (no loop-carried sums).
+template <int GS, int R, int W, bool KAHAN, bool SHORT>
+__device__ __forceinline__ bool consume_tile(fold_smem &sm, const fold_table &tb, int g0, int j,
+                                             int i0, int nE, unsigned use, bool all_used,
+                                             int nmin, uint32_t mine, best_slots bs, ring &rg) {
     constexpr int T = FT_THREADS * R;
-    constexpr uint32_t kRowStep = FT_THREADS * (uint32_t)sizeof(float2);
     const int c = threadIdx.x;
-    const uint32_t mine = ring0 + (uint32_t)c * (uint32_t)sizeof(float2);
-    float best_lr2[GS];
+    uint64_t acc[GS][R];
+    uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
+    // Epoch 0: every period's cell is its phase cell (o_0 = 0), one load for all. Epoch 1 then
+    // starts each sum as (epoch-0 cell + epoch-1 cell).
+    if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
+    uint64_t v0[R];
+    {
+        const uint32_t a = mine + rg.stage * rg.bytes;
+        lds_rows<0, R>(v0, a);
+        mbar_arrive(&sm.empty[rg.stage]);
+    }
+    rg.next();
+    if (KAHAN || nE < 2) {
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[gg][r] = v0[r];
+        if constexpr (KAHAN) {
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg)
+#pragma unroll
+                for (int r = 0; r < R; ++r) cmp[gg][r] = 0ull;
+        }
+    }
+    if (nE >= 2) {
+        if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
+        const uint32_t a = mine + rg.stage * rg.bytes;
+        epoch_offsets<GS, W> off;
+        off.load(tb.off + (uint32_t)(GS * W));
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            const uint32_t ag = a + off[gg];
+            uint64_t v[R];
+            lds_rows<0, R>(v, ag);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if constexpr (KAHAN)
+                    kahan_add_pair(acc[gg][r], cmp[gg][r], v[r]);
+                else
+                    acc[gg][r] = sum_pair(v0[r], v[r]);
+            }
+        }
+        mbar_arrive(&sm.empty[rg.stage]);
+        rg.next();
+    }
+    if constexpr (SHORT) {
+        if (nE >= 3) {
+            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
+            const uint32_t a = mine + rg.stage * rg.bytes;
+            epoch_offsets<GS, W> off;
+            off.load(tb.off + (uint32_t)(2 * GS * W));
+#pragma unroll
+            for (int gg = 0; gg < GS; ++gg) {
+                const uint32_t ag = a + off[gg];
+                uint64_t v[R];
+                lds_rows<0, R>(v, ag);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if constexpr (KAHAN)
+                        kahan_add_pair(acc[gg][r], cmp[gg][r], v[r]);
+                    else
+                        add_pair(acc[gg][r], v[r]);
+                }
+            }
+            mbar_arrive(&sm.empty[rg.stage]);
+            rg.next();
+        }
+    } else {
+        const bool ok =
+            all_used ? consume_epochs<GS, R, W, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg)
+                     : consume_epochs<GS, R, W, KAHAN, false>(sm, tb, nE, use, mine, acc, cmp, rg);
+        if (!ok) return false;
+    }
+    // 2 LR = SA^2 / SB per (period, phase); the running maximum keeps the first (smallest j,
+    // then smallest i) of equal values. Whole tiles (nmin: the phases every used period has)
+    // first run the candidate test over all their windows.
+    float m = i0 + T > nmin ? 1.0f : -1.0f;  // a ragged tile takes the exact comparisons
 #pragma unroll
     for (int gg = 0; gg < GS; ++gg) {
-        best_lr2[gg] = -1.0f;
-        best_at[gg * FT_THREADS + c] = 0u;
+        if (!all_used && !((use >> gg) & 1u)) continue;
+        const float h = bs.lr2[gg * FT_THREADS + c] * kCandidate;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            uint64_t v = acc[gg][r];
+            if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
+            float x, y;
+            split_pair(v, x, y);
+            m = fmaxf(m, fmaf(x, x, -(h * y)));
+        }
     }
+    if (m > 0.0f) {
+        const uint32_t jI = (uint32_t)j * (uint32_t)sm.it.I;
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg) {
+            if (!((use >> gg) & 1u)) continue;
+            const int nph = sm.nph[g0 + gg];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = i0 + c + r * FT_THREADS;
+                uint64_t v = acc[gg][r];
+                if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
+                float x, y;
+                split_pair(v, x, y);
+                if (i < nph)
+                    take_max(x, y, jI + (uint32_t)i, bs, gg);
+            }
+        }
+    }
+    return true;
+}
+
+template <int GS, int R, int W, bool KAHAN>
+__device__ void consume_main(fold_smem &sm, uint32_t ring0, best_slots bs, const fold_table &tb,
+                             int g0, int nph_sub, ring &rg) {
+    constexpr int T = FT_THREADS * R;
+    const int c = threadIdx.x;
+    const uint32_t mine = ring0 + (uint32_t)c * (uint32_t)sizeof(float2);
+    init_best<GS>(bs);
     for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
         const unsigned use = period_use<GS>(sm, g0, j);
         if (!use) continue;
         const bool all_used = use == (1u << GS) - 1u;
+        int nmin = nph_sub;  // phases every used period has
+#pragma unroll
+        for (int gg = 0; gg < GS; ++gg)
+            if ((use >> gg) & 1u) nmin = min(nmin, sm.nph[g0 + gg]);
         int nE = tb.Es;
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
             nE = live_epochs(tb, nE, sm.it.I, i0);
-            uint64_t acc[GS][R];
-            uint64_t cmp[KAHAN ? GS : 1][KAHAN ? R : 1];  // minus the Kahan compensation
-            // Epoch 0: every period's cell is its phase cell (o_0 = 0), one load for all.
-            // Epoch 1 then starts each sum as (epoch-0 cell + epoch-1 cell). (A wait that gave
-            // up ends the path at once: the main path has no block barrier, so every thread
-            // still meets the caller's next one.)
-            if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return;
-            uint64_t v0[R];
-            {
-                const uint32_t a = mine + rg.stage * rg.bytes;
-#pragma unroll
-                for (int r = 0; r < R; ++r) v0[r] = lds_pair(a + r * kRowStep);
-                mbar_arrive(&sm.empty[rg.stage]);
-            }
-            rg.next();
-            if (KAHAN || nE < 2) {
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[gg][r] = v0[r];
-                if constexpr (KAHAN) {
-#pragma unroll
-                    for (int gg = 0; gg < GS; ++gg)
-#pragma unroll
-                        for (int r = 0; r < R; ++r) cmp[gg][r] = 0ull;
-                }
-            }
-            if (nE >= 2) {
-                if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return;
-                const uint32_t a = mine + rg.stage * rg.bytes;
-                epoch_offsets<GS, W> off;
-                off.load(tb.off + (uint32_t)(GS * W));
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg) {
-                    const uint32_t ag = a + off[gg];
-                    uint64_t v[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = lds_pair(ag + r * kRowStep);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if constexpr (KAHAN)
-                            kahan_add_pair(acc[gg][r], cmp[gg][r], v[r]);
-                        else
-                            acc[gg][r] = sum_pair(v0[r], v[r]);
-                    }
-                }
-                mbar_arrive(&sm.empty[rg.stage]);
-                rg.next();
-            }
+            // (a wait that gave up ends the path at once: the main path has no block barrier,
+            // so every thread still meets the caller's next one)
             const bool ok =
-                all_used ? consume_epochs<GS, R, W, KAHAN, true>(sm, tb, nE, use, mine, acc, cmp, rg)
-                         : consume_epochs<GS, R, W, KAHAN, false>(sm, tb, nE, use, mine, acc, cmp, rg);
+                nE <= 3 ? consume_tile<GS, R, W, KAHAN, true>(sm, tb, g0, j, i0, nE, use, all_used,
+                                                              nmin, mine, bs, rg)
+                        : consume_tile<GS, R, W, KAHAN, false>(sm, tb, g0, j, i0, nE, use, all_used,
+                                                               nmin, mine, bs, rg);
             if (!ok) return;
-            // 2 LR = SA^2 / SB per (period, phase); the running maximum keeps the first
-            // (smallest j, then smallest i) of equal values. Whole tiles first run the
-            // candidate test over all their windows.
-            int nmin = nph_sub;  // phases every used period has
-#pragma unroll
-            for (int gg = 0; gg < GS; ++gg)
-                if ((use >> gg) & 1u) nmin = min(nmin, sm.nph[g0 + gg]);
-            bool any = i0 + T > nmin;
-            if (!any) {
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg) {
-                    if (!all_used && !((use >> gg) & 1u)) continue;
-                    const float h = best_lr2[gg] * kCandidate;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        uint64_t v = acc[gg][r];
-                        if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
-                        float x, y;
-                        split_pair(v, x, y);
-                        any |= x * x > h * y;
-                    }
-                }
-            }
-            if (any) {
-                const uint32_t jI = (uint32_t)j * (uint32_t)sm.it.I;
-#pragma unroll
-                for (int gg = 0; gg < GS; ++gg) {
-                    if (!((use >> gg) & 1u)) continue;
-                    const int nph = sm.nph[g0 + gg];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const int i = i0 + c + r * FT_THREADS;
-                        uint64_t v = acc[gg][r];
-                        if constexpr (KAHAN) add_pair(v, cmp[gg][r]);
-                        float x, y;
-                        split_pair(v, x, y);
-                        if (i < nph)
-                            take_max(x, y, jI + (uint32_t)i, best_lr2[gg],
-                                     &best_at[gg * FT_THREADS + c]);
-                    }
-                }
-            }
         }
     }
-    publish_best<GS>(sm, g0, best_lr2, best_at);
+    publish_best<GS>(sm, g0, bs);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -520,7 +574,7 @@ __device__ void produce_sliced(fold_smem &sm, uint32_t ring0, const fold_table &
 }
 
 template <int GS, int R, int W, bool KAHAN>
-__device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, uint32_t *best_at,
+__device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, best_slots bs,
                                const fold_table &tb, int g0, int Tp, ring &rg) {
     constexpr int T = FT_THREADS * R;
     const int H = T / Tp;
@@ -533,12 +587,7 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
         slice[r] = L / Tp;
         phase[r] = L - slice[r] * Tp;
     }
-    float best_lr2[GS];
-#pragma unroll
-    for (int gg = 0; gg < GS; ++gg) {
-        best_lr2[gg] = -1.0f;
-        best_at[gg * FT_THREADS + c] = 0u;
-    }
+    init_best<GS>(bs);
     for (int j = sm.it.jlo; j < sm.it.jhi; ++j) {
         const unsigned use = period_use<GS>(sm, g0, j);
         if (!use) continue;
@@ -603,13 +652,12 @@ __device__ void consume_sliced(fold_smem &sm, uint32_t ring0, uint64_t *part, ui
                 float x, y;
                 split_pair(v, x, y);
                 if (phi < nph && y > 0.0f)
-                    take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)phi, best_lr2[gg],
-                             &best_at[gg * FT_THREADS + c]);
+                    take_max(x, y, (uint32_t)j * (uint32_t)I + (uint32_t)phi, bs, gg);
             }
             block_sync();
         }
     }
-    publish_best<GS>(sm, g0, best_lr2, best_at);
+    publish_best<GS>(sm, g0, bs);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -731,40 +779,39 @@ __device__ __forceinline__ void build_table_w(fold_smem &sm, unsigned char *raw,
 
 template <int GS, int R, int W, bool KAHAN>
 __device__ void fold_subgroup(fold_smem &sm, uint32_t ring0, const fold_table &tb, uint64_t *part,
-                              uint32_t *best_at, bool sliced, int Tp, int g0, int nph_sub,
-                              ring &rg) {
+                              best_slots bs, bool sliced, int Tp, int g0, int nph_sub, ring &rg) {
     const bool producer = threadIdx.x >= FT_THREADS;
     if (sliced) {
         if (producer)
             produce_sliced<GS, R>(sm, ring0, tb, g0, Tp, rg);
         else
-            consume_sliced<GS, R, W, KAHAN>(sm, ring0, part, best_at, tb, g0, Tp, rg);
+            consume_sliced<GS, R, W, KAHAN>(sm, ring0, part, bs, tb, g0, Tp, rg);
     } else if (producer) {
         // the main path has no block barrier: the producer's first lane runs it alone
         if ((threadIdx.x & 31) == 0) produce_main<GS, R>(sm, ring0, tb, g0, nph_sub, rg);
         __syncwarp();
     } else {
-        consume_main<GS, R, W, KAHAN>(sm, ring0, best_at, tb, g0, nph_sub, rg);
+        consume_main<GS, R, W, KAHAN>(sm, ring0, bs, tb, g0, nph_sub, rg);
     }
 }
 
 template <int GS, int R, bool KAHAN>
 __device__ __forceinline__ void fold_subgroup_w(fold_smem &sm, uint32_t ring0,
                                                 const fold_table &tb, uint64_t *part,
-                                                uint32_t *best_at, bool sliced, int Tp, int g0,
+                                                best_slots bs, bool sliced, int Tp, int g0,
                                                 int nph_sub, ring &rg, int W) {
     if (W == 4)
-        fold_subgroup<GS, R, 4, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg);
+        fold_subgroup<GS, R, 4, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg);
     else
-        fold_subgroup<GS, R, 2, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg);
+        fold_subgroup<GS, R, 2, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg);
 }
 
 // Fold the group whose slot metadata and work item are in `sm` (all threads): every sub-group
 // (8 -> 4 -> 2 -> 1 periods, as the table allows) in turn; slot g's best key ends in
 // sm.best[g]. A wait that gave up leaves sm.abort set.
 template <bool KAHAN, int R>
-__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab,
-                           uint32_t *best_at, ring &rg) {
+__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab, best_slots bs,
+                           ring &rg) {
     constexpr int T = FT_THREADS * R;
     for (int g0 = 0; g0 < FT_G;) {
         int GS = FT_G;
@@ -832,13 +879,13 @@ __device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab
         uint64_t *part = reinterpret_cast<uint64_t *>(raw + (ns - 1) * stage_bytes);
         const uint32_t ring0 = smem_u32(raw);
         if (GS == 8)
-            fold_subgroup_w<8, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
+            fold_subgroup_w<8, R, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg, W);
         else if (GS == 4)
-            fold_subgroup_w<4, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
+            fold_subgroup_w<4, R, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg, W);
         else if (GS == 2)
-            fold_subgroup_w<2, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
+            fold_subgroup_w<2, R, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg, W);
         else
-            fold_subgroup_w<1, R, KAHAN>(sm, ring0, tb, part, best_at, sliced, Tp, g0, nph_sub, rg, W);
+            fold_subgroup_w<1, R, KAHAN>(sm, ring0, tb, part, bs, sliced, Tp, g0, nph_sub, rg, W);
         g0 += GS;
     }
 }
@@ -864,11 +911,12 @@ __device__ void drain_copies(fold_smem &sm, const ring &rg) {
     for (int s = 0; s < FT_NSTAGE; ++s) mbar_wait(&sm.full[s], ((rg.par >> s) & 1u) ^ 1u);
 }
 
-// Dynamic shared memory: the strip ring, the epoch table, the per-thread argmax indices.
+// Dynamic shared memory: the strip ring, the epoch table, the consumers' running maxima.
 __device__ __forceinline__ void fold_smem_views(unsigned char *raw, unsigned char *&tab,
-                                                uint32_t *&best_at) {
+                                                best_slots &bs) {
     tab = raw + FT_RING_BYTES;
-    best_at = reinterpret_cast<uint32_t *>(tab + FT_TAB_BYTES);
+    bs.lr2 = reinterpret_cast<float *>(tab + FT_TAB_BYTES);
+    bs.at = reinterpret_cast<uint32_t *>(bs.lr2 + FT_G * FT_THREADS);
 }
 
 // Single light curve. Work item = (duration chunk, group); chunks outermost so that the blocks
@@ -885,8 +933,8 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ fold_smem sm;
     unsigned char *tab;
-    uint32_t *best_at;
-    fold_smem_views(smem_raw, tab, best_at);
+    best_slots bs;
+    fold_smem_views(smem_raw, tab, bs);
     const int t = threadIdx.x;
     const int jc = blockIdx.x / n_groups;
     const int grp = n_groups - 1 - (int)(blockIdx.x % n_groups);
@@ -908,7 +956,7 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
     block_sync();
     ring rg;
     constexpr int R = KAHAN ? FT_R / 2 : FT_R;
-    fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, rg);
+    fold_group<KAHAN, R>(sm, smem_raw, tab, bs, rg);
     block_sync();
     if (sm.abort) {
         drain_copies(sm, rg);
@@ -941,8 +989,8 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
     // the queue length: n_items, or the count a device-side selection left (capped by n_items)
     if (n_items_dev) n_items = min(n_items, (int64_t)*n_items_dev);
     unsigned char *tab;
-    uint32_t *best_at;
-    fold_smem_views(smem_raw, tab, best_at);
+    best_slots bs;
+    fold_smem_views(smem_raw, tab, bs);
     const int t = threadIdx.x;
     fold_init_barriers(sm);
     ring rg;
@@ -974,7 +1022,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                            cv.I, c, p, q);
         }
         block_sync();
-        fold_group<KAHAN, R>(sm, smem_raw, tab, best_at, rg);
+        fold_group<KAHAN, R>(sm, smem_raw, tab, bs, rg);
         block_sync();
         if (sm.abort) {
             drain_copies(sm, rg);
@@ -993,7 +1041,8 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
 }  // namespace
 
 size_t fold_smem_bytes() {
-    return (size_t)FT_RING_BYTES + (size_t)FT_TAB_BYTES + (size_t)FT_G * FT_THREADS * sizeof(uint32_t);
+    return (size_t)FT_RING_BYTES + (size_t)FT_TAB_BYTES +
+           (size_t)FT_G * FT_THREADS * (sizeof(float) + sizeof(uint32_t));
 }
 
 cudaError_t fold_configure() {
