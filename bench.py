@@ -67,8 +67,9 @@ def parse():
                     help="plain FP32 sums or the Kahan-compensated precision form")
     ap.add_argument("--batch-curves", type=int, default=0,
                     help="measure the batched form on this many 30-min multi-sector curves")
-    ap.add_argument("--plain-curves", type=int, default=32,
-                    help="curves searched one at a time for the plain-form comparison")
+    ap.add_argument("--plain-curves", type=int, default=0,
+                    help="curves searched one at a time for the plain-form comparison "
+                         "(0: every curve of the batch)")
     ap.add_argument("--proposal", action="store_true",
                     help="the learned period-interval proposal: train the CNN on injection "
                          "curves, then search held-out curves with it and with the full fold")
@@ -304,7 +305,7 @@ def run_batch(args):
                              precision=args.precision)
     e2e_s = time.perf_counter() - t2
     # the plain per-curve GPU form on the first curves, same period grids
-    m = min(args.plain_curves, len(ws))
+    m = min(args.plain_curves, len(ws)) if args.plain_curves > 0 else len(ws)
     dmin = float(np.min(durs))
     torch.cuda.synchronize(dev)
     t3 = time.perf_counter()

@@ -322,7 +322,8 @@ typedef struct {
     int64_t fold_cell_reads; /* algorithmic (A, B) reads of the fold */
     size_t device_bytes;  /* device memory the batch holds */
     int32_t linear_threads;  /* chosen linear block size */
-    int32_t fold_variant;    /* chosen fold variant (phases per thread, blocks per SM) */
+    int32_t fold_variant;    /* chosen fold shape: bit 0 set = 2 phases per thread (else 4),
+                                bit 1 set = at most 4 periods folded together (else 8) */
     int32_t fold_blocks;     /* persistent fold blocks */
     int32_t graph;           /* 1 once the run is captured as a CUDA graph */
     double cadence;          /* shared resample cadence c (days) */

@@ -6,10 +6,16 @@
 // durations and the template, hence one set of window tables (a plan built from the first
 // curve). Each curve has its own time span (t_ref, grid length, t0 count) and period grid.
 //
+// Work order of the fold: the curves by decreasing t0 count (the largest first), each curve's
+// 8-period groups from its longest periods down, so that the queue ends with its cheapest
+// items; a curve's items stay together, so the blocks running at the same time read few
+// curves' grids (the L2 holds them).
+//
 // Autotuning (optional, at creation): the linear stage is timed with 128- and 64-thread
-// blocks and the fold with 4 and 2 phases per thread on a sample of its work items; the
-// fastest of each is kept. The chosen sequence of memsets and kernels is captured once into
-// a CUDA graph on the batch's own stream and replayed by every run.
+// blocks (t0 outputs per block), and the fold in its four shapes (4 or 2 phases per thread,
+// sub-groups of at most 8 or 4 periods per block) on a sample of work items spread over the
+// whole queue; the fastest of each is kept. The chosen sequence of memsets and kernels is
+// captured once into a CUDA graph on the batch's own stream and replayed by every run.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -42,6 +48,8 @@ struct cetra_batch {
     cetra_best *d_best = nullptr;
     int *d_queue = nullptr, *d_status = nullptr;
     int64_t *d_items = nullptr;  // explicit fold work list (cetra_batch_run_items)
+    int64_t *d_order_off = nullptr;   // queue order: items before each curve of the order
+    int32_t *d_order_curve = nullptr;  // queue order: the curves, largest first
     unsigned char *d_flags = nullptr;        // one byte per work item (proposal selection)
     unsigned long long *d_counts = nullptr;  // selected items, their periods
 };
@@ -126,22 +134,26 @@ cudaError_t enqueue_fold(cetra_batch *b, int64_t n_items, int fold_variant,
     if ((e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(int), st))) return e;  // queue, status
     if ((e = launch_batch_fold(st, b->fold_blocks, fold_variant, plan, b->d_ab, b->d_curves,
                                b->d_group_off, b->n_curves, n_items, b->d_queue, b->d_pkeys,
-                               b->d_keys, b->d_status, item_list, n_items_dev)))
+                               b->d_keys, b->d_status, item_list, n_items_dev, b->d_order_off,
+                               b->d_order_curve)))
         return e;
     return launch_batch_finalize(st, plan, b->d_ab, b->d_curves, b->n_curves, b->d_pkeys,
                                  b->d_keys, b->d_status, b->d_best);
 }
 
-cudaError_t enqueue(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads) {
+cudaError_t enqueue(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads,
+                    const int64_t *item_list = nullptr) {
     cudaError_t e = enqueue_linear(b, lin_threads);
     if (e) return e;
-    return enqueue_fold(b, n_items, fold_variant, nullptr);
+    return enqueue_fold(b, n_items, fold_variant, item_list);
 }
 
-// Milliseconds of one enqueue() with the given shapes (the batch is rebuilt by the caller).
-int time_once(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads, float *ms) {
+// Milliseconds of one enqueue() with the given shapes (the batch is rebuilt by the caller);
+// item_list: the fold's work items (NULL: the queue order).
+int time_once(cetra_batch *b, int64_t n_items, int fold_variant, int lin_threads, float *ms,
+              const int64_t *item_list = nullptr) {
     cudaError_t e = cudaEventRecord(b->ev_start, b->stream);
-    if (!e) e = enqueue(b, n_items, fold_variant, lin_threads);
+    if (!e) e = enqueue(b, n_items, fold_variant, lin_threads, item_list);
     if (!e) e = cudaEventRecord(b->ev_stop, b->stream);
     if (!e) e = cudaEventSynchronize(b->ev_stop);
     if (!e) e = cudaEventElapsedTime(ms, b->ev_start, b->ev_stop);
@@ -176,16 +188,22 @@ int autotune(cetra_batch *b) {
     int rc = upload_tiles(b);
     if (rc) return rc;
     if (b->plan->precision == CETRA_FP32_KAHAN) return CETRA_OK;  // one fold shape
-    // fold shape: time a sample of the work items (the first ones: the longest periods of
-    // the first curves, a fair mix of group widths) with each variant
+    // fold shape: time a sample of work items spread evenly over the whole batch (every
+    // stride-th item: all curve lengths, all period ranges) with each variant
     const int64_t sample = std::min<int64_t>(b->n_items, (int64_t)b->fold_blocks * 8);
+    if (sample <= 0) return CETRA_OK;
+    std::vector<int64_t> picks((size_t)sample);
+    for (int64_t x = 0; x < sample; ++x) picks[(size_t)x] = x * b->n_items / sample;
+    cudaError_t ce = cudaMemcpy(b->d_items, picks.data(), (size_t)sample * sizeof(int64_t),
+                                cudaMemcpyHostToDevice);
+    if (ce) return cuda_fail(b->ctx, ce, "batch autotune sample");
     float base = 0.f;
     if ((rc = time_once(b, 0, 0, best_threads, &base))) return rc;
     float best_fold = 0.f;
     for (int v = 0; v < batch_fold_variants(); ++v) {
         float ms = 0.f;
-        if ((rc = time_once(b, sample, v, best_threads, &ms))) return rc;
-        if ((rc = time_once(b, sample, v, best_threads, &ms))) return rc;
+        if ((rc = time_once(b, sample, v, best_threads, &ms, b->d_items))) return rc;
+        if ((rc = time_once(b, sample, v, best_threads, &ms, b->d_items))) return rc;
         ms -= base;
         if (v == 0 || ms < best_fold) {
             best_fold = ms;
@@ -331,6 +349,10 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_items = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1) * sizeof(int64_t));
     o_flags = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1));
     o_cnt = off; off = up(off + 2 * sizeof(unsigned long long));
+    const size_t o_ooff = off;
+    off = up(off + (size_t)(n_curves + 1) * sizeof(int64_t));
+    const size_t o_ocur = off;
+    off = up(off + (size_t)n_curves * sizeof(int32_t));
     device_guard dguard(ctx->device);
     cudaError_t e = dguard.status;
     if (e) return bail(cuda_fail(ctx, e, "batch device"));
@@ -359,6 +381,20 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     b->d_items = reinterpret_cast<int64_t *>(base + o_items);
     b->d_flags = reinterpret_cast<unsigned char *>(base + o_flags);
     b->d_counts = reinterpret_cast<unsigned long long *>(base + o_cnt);
+    b->d_order_off = reinterpret_cast<int64_t *>(base + o_ooff);
+    b->d_order_curve = reinterpret_cast<int32_t *>(base + o_ocur);
+    // queue order: curves by decreasing t0 count (ties: curve index)
+    std::vector<int32_t> order((size_t)n_curves);
+    for (int cidx = 0; cidx < n_curves; ++cidx) order[(size_t)cidx] = cidx;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return b->curves[(size_t)x].I > b->curves[(size_t)y].I;
+    });
+    std::vector<int64_t> order_off((size_t)n_curves + 1, 0);
+    for (int k = 0; k < n_curves; ++k) {
+        const int32_t cidx = order[(size_t)k];
+        order_off[(size_t)k + 1] =
+            order_off[(size_t)k] + (b->group_off[(size_t)cidx + 1] - b->group_off[(size_t)cidx]);
+    }
 
     if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) ||
         (e = cudaEventCreate(&b->ev_start)) || (e = cudaEventCreate(&b->ev_stop)))
@@ -372,6 +408,10 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
         (e = cudaMemcpy(b->d_group_off, b->group_off.data(), b->group_off.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(b->d_curves, b->curves.data(), b->curves.size() * sizeof(batch_curve),
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_order_off, order_off.data(), order_off.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_order_curve, order.data(), order.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)))
         return bail(cuda_fail(ctx, e, "batch upload"));
     if ((e = batch_configure(plan))) return bail(cuda_fail(ctx, e, "batch configure"));

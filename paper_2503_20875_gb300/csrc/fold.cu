@@ -130,6 +130,7 @@ struct fold_item {
     int *status;
     int64_t ld;
     int I, J, jlo, jhi, mask_k0;
+    int gmax;  // largest sub-group (periods folded together), a power of two <= FT_G
 };
 
 struct fold_smem {
@@ -814,7 +815,7 @@ __device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab
                            ring &rg) {
     constexpr int T = FT_THREADS * R;
     for (int g0 = 0; g0 < FT_G;) {
-        int GS = FT_G;
+        int GS = sm.it.gmax;
         while (g0 % GS) GS >>= 1;
         int Es = 0, W = 4;
         bool table_ok = false;
@@ -951,6 +952,7 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
         sm.it.jlo = jc * jchunk;
         sm.it.jhi = min(J, sm.it.jlo + jchunk);
         sm.it.mask_k0 = k0;
+        sm.it.gmax = FT_G;
     }
     if (t < FT_G) fold_slot_meta(sm, t, k0 + t < K, k0 + t < K ? periods[k0 + t] : 0.0, I, c, p, q);
     block_sync();
@@ -974,6 +976,9 @@ fold_kernel(const float2 *__restrict__ ab, int I, int64_t ld, int J,
 // Batched form: persistent blocks drain a queue of (curve, group of FT_G periods) items; each
 // group's best per period goes into the curve's key (LR bits, inverted period index: the
 // largest LR wins, ties to the smallest period index).
+// Queue order (item_list NULL): the curves in the order order_curve[] (largest first), each
+// curve's groups from its longest periods down, so that the last items of the queue are the
+// cheapest; order_off is the prefix count of items over that order.
 template <bool KAHAN, int R>
 __global__ void __launch_bounds__(FT_BLOCK, FT_MIN_BLOCKS)
 batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__ curves,
@@ -982,7 +987,9 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
                   int *__restrict__ queue, unsigned long long *__restrict__ period_keys,
                   unsigned long long *__restrict__ curve_keys, int *__restrict__ status,
                   const int64_t *__restrict__ item_list,
-                  const unsigned long long *__restrict__ n_items_dev) {
+                  const unsigned long long *__restrict__ n_items_dev,
+                  const int64_t *__restrict__ order_off, const int32_t *__restrict__ order_curve,
+                  int gmax) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ fold_smem sm;
     __shared__ int s_item;
@@ -999,8 +1006,15 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
         if (t == 0) s_item = atomicAdd(queue, 1);
         block_sync();
         if (s_item >= n_items) break;
-        // queue position -> work item: the position itself, or the caller's list entry
-        const int64_t item = item_list ? item_list[s_item] : (int64_t)s_item;
+        // queue position -> work item: the caller's list entry, or the position in the order
+        int64_t item;
+        if (item_list) {
+            item = item_list[s_item];
+        } else {
+            const int oc = csr_find(order_off, n_curves, (int64_t)s_item);
+            const int cc = order_curve[oc];
+            item = group_off[cc] + (order_off[oc + 1] - 1 - (int64_t)s_item);
+        }
         const int cidx = csr_find(group_off, n_curves, item);
         const batch_curve cv = curves[cidx];
         const int k0 = (int)(item - group_off[cidx]) * FT_G;
@@ -1015,6 +1029,7 @@ batch_fold_kernel(const float2 *__restrict__ ab, const batch_curve *__restrict__
             sm.it.jlo = 0;
             sm.it.jhi = J;
             sm.it.mask_k0 = 0;
+            sm.it.gmax = gmax;
         }
         if (t < FT_G) {
             const bool present = k0 + t < cv.n_periods;
@@ -1084,8 +1099,10 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
     return cudaGetLastError();
 }
 
-// Fold variants the autotuner chooses from: phases per thread (FT_R or FT_R / 2).
-int batch_fold_variants() { return 2; }
+// Fold variants the autotuner chooses from: bit 0 set = FT_R / 2 phases per thread (else
+// FT_R), bit 1 set = sub-groups of at most FT_G / 2 periods (else FT_G). The compensated form
+// always takes FT_R / 2 phases per thread.
+int batch_fold_variants() { return 4; }
 int batch_fold_blocks_per_sm(int) { return FT_MIN_BLOCKS; }
 
 cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
@@ -1093,15 +1110,18 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
                               unsigned long long *curve_keys, int *status,
-                              const int64_t *item_list, const unsigned long long *n_items_dev) {
+                              const int64_t *item_list, const unsigned long long *n_items_dev,
+                              const int64_t *order_off, const int32_t *order_curve) {
     if (n_items <= 0) return cudaSuccess;
     auto kern = batch_fold_kernel<false, FT_R>;
     if (plan->precision == CETRA_FP32_KAHAN)
         kern = batch_fold_kernel<true, FT_R / 2>;
-    else if (variant == 1)
+    else if (variant & 1)
         kern = batch_fold_kernel<false, FT_R / 2>;
+    const int gmax = (variant & 2) ? FT_G / 2 : FT_G;
     kern<<<blocks, FT_BLOCK, fold_smem_bytes(), stream>>>(
         ab, curves, group_off, n_curves, n_items, plan->J, plan->d_durations, plan->cadence,
-        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list, n_items_dev);
+        plan->p, plan->q, queue, period_keys, curve_keys, status, item_list, n_items_dev,
+        order_off, order_curve, gmax);
     return cudaGetLastError();
 }

@@ -191,8 +191,8 @@ cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, cons
                               const int64_t *group_off, int n_curves, int64_t n_items,
                               int *queue, unsigned long long *period_keys,
                               unsigned long long *curve_keys, int *status,
-                              const int64_t *item_list,
-                              const unsigned long long *n_items_dev = nullptr);
+                              const int64_t *item_list, const unsigned long long *n_items_dev,
+                              const int64_t *order_off, const int32_t *order_curve);
 // Self-test of the bounded barrier wait (kernels.cu): d_out[0] = 1 if the wait gave up,
 // d_out[1] its duration in units of 2^20 SM clocks (d_out may be NULL); a wait that gave up
 // also stores CETRA_ETIMEOUT in *d_status, as the fold does (d_status may be NULL).
