@@ -76,7 +76,11 @@ def parse():
     ap.add_argument("--proposal-train", type=int, default=200000)
     ap.add_argument("--proposal-eval", type=int, default=8192)
     ap.add_argument("--proposal-epochs", type=int, default=2)
-    ap.add_argument("--proposal-frac", type=float, default=0.05)
+    ap.add_argument("--proposal-frac", type=float, default=0.05,
+                    help="fraction of period intervals the proposal keeps (the headline point)")
+    ap.add_argument("--proposal-sweep", default="0.05,0.1,0.2,0.4,0.6,0.8",
+                    help="comma list of kept fractions: recall and curves/s at each, and the "
+                         "smallest fraction whose recall equals the full search's")
     ap.add_argument("--neighbours", action="store_true",
                     help="single-transit search of the 4-yr 1-min curve and the three-round "
                          "search-and-mask of the 20-s TESS curve")
@@ -437,10 +441,9 @@ def run_proposal(args):
     full = eb.run()
     t_full = time.perf_counter() - t2
 
-    def proposed(make_map):
-        """features -> map -> comb -> selection + fold; wall time of each stage (each ends
+    def map_scores(make_map):
+        """features -> map -> comb: the per-interval scores; wall time of each stage (each ends
         in a synchronisation)."""
-        split = {}
         torch.cuda.synchronize(dev)
         ta = time.perf_counter()
         d_f = eb.features(n_bins)  # resample + linear + max-pool (blocks)
@@ -451,26 +454,52 @@ def run_proposal(args):
         scores = proposal.interval_scores(ctx, geo, eb.info, m, p_hi)
         torch.cuda.synchronize(dev)
         td = time.perf_counter()
-        best, n_it, n_per = eb.run_proposed(scores, proposal.P_LO, p_hi, args.proposal_frac)
-        te = time.perf_counter()
-        split = {"features_ms": 1e3 * (tb - ta), "map_ms": 1e3 * (tc - tb),
-                 "comb_ms": 1e3 * (td - tc), "select_fold_ms": 1e3 * (te - td)}
-        return best, n_per, te - ta, split
+        return scores, td - ta, {"features_ms": 1e3 * (tb - ta), "map_ms": 1e3 * (tc - tb),
+                                 "comb_ms": 1e3 * (td - tc)}
 
-    proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))  # warm-up
-    best_l, per_l, t_prop, split_l = proposed(lambda d_f: proposal.learned_map(ctx, infer, d_f))
-    best_s, per_s, _, _ = proposed(lambda d_f: proposal.lr_map(ctx, d_f))
-    rnd = torch.rand((eb.n, proposal.N_INTERVALS), generator=torch.Generator().manual_seed(5))
-    best_r, _, per_r = eb.run_proposed(rnd.to(dev), proposal.P_LO, p_hi, args.proposal_frac)
+    def select_fold(scores, frac):
+        """device-side choice of the top intervals and the fold of their periods (timed)."""
+        torch.cuda.synchronize(dev)
+        ta = time.perf_counter()
+        best, _, n_per = eb.run_proposed(scores, proposal.P_LO, p_hi, frac)
+        return best, n_per, time.perf_counter() - ta
+
     n_inj = sum(1 for p in planets if p)
 
     def rec(best):
         return int(sum(recovered(best["period"][c], planets[c]) for c in range(eb.n)))
 
+    learned = lambda d_f: proposal.learned_map(ctx, infer, d_f)
+    sc_w, _, _ = map_scores(learned)  # warm-up
+    select_fold(sc_w, args.proposal_frac)
+    sc_l, t_map_l, split_l = map_scores(learned)
+    sc_s, t_map_s, _ = map_scores(lambda d_f: proposal.lr_map(ctx, d_f))
+    rnd = torch.rand((eb.n, proposal.N_INTERVALS), generator=torch.Generator().manual_seed(5)).to(dev)
+    rec_full = rec(full)
+    fracs = sorted({args.proposal_frac} | {float(x) for x in args.proposal_sweep.split(",") if x})
+    sweep = []
+    for frac in fracs:
+        best_l, per_l, t_sel_l = select_fold(sc_l, frac)
+        best_s, per_s, t_sel_s = select_fold(sc_s, frac)
+        t_prop = t_map_l + t_sel_l
+        point = {"top_frac": frac, "value": n_eval / t_prop, "unit": UNIT,
+                 "ms": 1e3 * t_prop, "select_fold_ms": 1e3 * t_sel_l,
+                 "speedup": t_full / t_prop,
+                 "recall": {"learned": rec(best_l), "lr_only": rec(best_s)},
+                 "lr_only_value": n_eval / (t_map_s + t_sel_s),
+                 "periods_folded": {"learned": per_l / total, "lr_only": per_s / total}}
+        if frac == args.proposal_frac:  # random intervals: the headline point only
+            best_r, per_r, _ = select_fold(rnd, frac)
+            point["recall"]["random"] = rec(best_r)
+            point["periods_folded"]["random"] = per_r / total
+        sweep.append(point)
+    head = next(x for x in sweep if x["top_frac"] == args.proposal_frac)
+    equal = [x for x in sweep if x["recall"]["learned"] >= rec_full]
+    split_l = dict(split_l, select_fold_ms=head["select_fold_ms"])
     line = {"metric": "learned proposal: light curves searched/s vs the full periodic search, "
                       "at injected-planet recall",
-            "value": n_eval / t_prop, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * t_prop, "higher_is_better": True, "scaling": "weak",
+            "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (CNN: bf16 weights, f32 sums)", "data": "synthetic",
             "config": {"workload": f"batch_30min_{n_eval} held out (1-13 sectors, 30 % planets)",
                        "cnn": "4 conv1d layers, 32 channels, k 9", "bins": n_bins,
@@ -478,12 +507,15 @@ def run_proposal(args):
                        "n_periods": int(total)},
             "full_search": {"value": n_eval / t_full, "unit": UNIT, "ms": 1e3 * t_full},
             "proposal_split": split_l,
-            "speedup": t_full / t_prop,
+            "speedup": head["speedup"],
             "recall": {"criterion": "1 % of P, P/2 or 2P", "injected": n_inj,
-                       "full": rec(full), "learned": rec(best_l), "lr_only": rec(best_s),
-                       "random": rec(best_r)},
-            "periods_folded": {"learned": per_l / total, "lr_only": per_s / total,
-                               "random": per_r / total},
+                       "full": rec_full, **head["recall"]},
+            "periods_folded": head["periods_folded"],
+            "sweep": sweep,
+            "equal_recall": ({"top_frac": equal[0]["top_frac"], "value": equal[0]["value"],
+                              "speedup": equal[0]["speedup"]} if equal else
+                             {"top_frac": None, "note": "no swept fraction recovers as many "
+                              "injected planets as the full search"}),
             "train": {"curves": n_train, "with_planet": n_planets, "points": n_points,
                       "epochs": args.proposal_epochs, "loss": [round(h, 5) for h in hist],
                       "data_s": t_data, "data_split": split, "train_s": t_train,
