@@ -40,7 +40,8 @@ struct cetra_batch {
     void *d_mem = nullptr;
     size_t d_bytes = 0;
     double *d_time = nullptr;
-    float *d_flux = nullptr, *d_err = nullptr, *d_wy = nullptr, *d_w = nullptr;
+    float *d_flux = nullptr, *d_err = nullptr;
+    float2 *d_grid = nullptr;  // interleaved (W y, W) cells of every curve
     float2 *d_ab = nullptr;
     int64_t *d_pt_off = nullptr, *d_tile_off = nullptr, *d_group_off = nullptr;
     batch_curve *d_curves = nullptr;
@@ -110,15 +111,15 @@ cudaError_t enqueue_linear(cetra_batch *b, int lin_threads) {
     cetra_plan *plan = b->plan;
     cudaStream_t st = b->stream;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(b->d_wy, 0, (size_t)b->n_cells * sizeof(float), st))) return e;
-    if ((e = cudaMemsetAsync(b->d_w, 0, (size_t)b->n_cells * sizeof(float), st))) return e;
+    if ((e = cudaMemsetAsync(b->d_grid, 0, (size_t)b->n_cells * sizeof(float2), st))) return e;
+    if ((e = cudaMemsetAsync(b->d_status + 1, 0, sizeof(int), st))) return e;  // linear status
     if ((e = cudaMemsetAsync(b->d_ab, 0, (size_t)b->ab_cells * sizeof(float2), st))) return e;
     if ((e = launch_batch_resample(st, b->ctx->num_sms, plan, b->d_time, b->d_flux, b->d_err,
-                                   b->n_points, b->d_pt_off, b->n_curves, b->d_curves, b->d_wy,
-                                   b->d_w)))
+                                   b->n_points, b->d_pt_off, b->n_curves, b->d_curves,
+                                   b->d_grid)))
         return e;
     return launch_batch_linear(st, plan, lin_threads, b->d_tile_off, b->n_curves, b->n_tiles,
-                               b->d_curves, b->d_wy, b->d_w, b->d_ab);
+                               b->d_curves, b->d_grid, b->d_ab, b->d_status + 1);
 }
 
 // The fold over n_items work items (item_list NULL: items 0 .. n_items-1; n_items_dev not
@@ -314,7 +315,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
         cv.grid_off = grid;
         cv.ab_off = abc;
         cv.per_off = per;
-        grid += cv.n_grid;
+        grid += (cv.n_grid + 1) & ~1;  // each curve's cells start on a 16-byte boundary
         abc += (int64_t)n_dur * cv.ld;
         t0s += cv.I;
         per += cv.n_periods;
@@ -330,13 +331,12 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
 
     // device memory, one allocation carved in 256-byte aligned pieces
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off = 0, o_time, o_flux, o_err, o_wy, o_w, o_ab, o_pt, o_tile, o_grp, o_cv, o_keys,
+    size_t off = 0, o_time, o_flux, o_err, o_grid, o_ab, o_pt, o_tile, o_grp, o_cv, o_keys,
                     o_pkeys, o_best, o_q, o_items, o_flags, o_cnt;
     o_time = off; off = up(off + (size_t)n_points * sizeof(double));
     o_flux = off; off = up(off + (size_t)n_points * sizeof(float));
     o_err = off; off = up(off + (size_t)n_points * sizeof(float));
-    o_wy = off; off = up(off + (size_t)grid * sizeof(float));
-    o_w = off; off = up(off + (size_t)grid * sizeof(float));
+    o_grid = off; off = up(off + (size_t)grid * sizeof(float2));
     o_ab = off; off = up(off + (size_t)abc * sizeof(float2));
     o_pt = off; off = up(off + (size_t)(n_curves + 1) * sizeof(int64_t));
     o_tile = off; off = up(off + (size_t)(n_curves + 1) * sizeof(int64_t));
@@ -345,7 +345,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     o_keys = off; off = up(off + (size_t)n_curves * sizeof(unsigned long long));
     o_pkeys = off; off = up(off + (size_t)std::max<int64_t>(per, 1) * sizeof(unsigned long long));
     o_best = off; off = up(off + (size_t)n_curves * sizeof(cetra_best));
-    o_q = off; off = up(off + 2 * sizeof(int));
+    o_q = off; off = up(off + 3 * sizeof(int));  // queue, fold status, linear status
     o_items = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1) * sizeof(int64_t));
     o_flags = off; off = up(off + (size_t)std::max<int64_t>(b->n_items, 1));
     o_cnt = off; off = up(off + 2 * sizeof(unsigned long long));
@@ -366,8 +366,7 @@ int cetra_batch_create(cetra_ctx *ctx, const cetra_params *params, int n_curves,
     b->d_time = reinterpret_cast<double *>(base + o_time);
     b->d_flux = reinterpret_cast<float *>(base + o_flux);
     b->d_err = reinterpret_cast<float *>(base + o_err);
-    b->d_wy = reinterpret_cast<float *>(base + o_wy);
-    b->d_w = reinterpret_cast<float *>(base + o_w);
+    b->d_grid = reinterpret_cast<float2 *>(base + o_grid);
     b->d_ab = reinterpret_cast<float2 *>(base + o_ab);
     b->d_pt_off = reinterpret_cast<int64_t *>(base + o_pt);
     b->d_tile_off = reinterpret_cast<int64_t *>(base + o_tile);
@@ -450,14 +449,14 @@ int cetra_batch_run(cetra_ctx *ctx, cetra_batch *b, cetra_best *best) {
         (e = cudaGraphLaunch(b->graph, b->stream)))
         return cuda_fail(ctx, e, "batch graph launch");
     ctx->launches += 4;
-    int status = 0;
+    int status[2] = {0, 0};  // fold, linear stage
     if (best && (e = cudaMemcpyAsync(best, b->d_best, (size_t)b->n_curves * sizeof(cetra_best),
                                      cudaMemcpyDeviceToHost, b->stream)))
         return cuda_fail(ctx, e, "batch results");
-    if ((e = cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream)) ||
+    if ((e = cudaMemcpyAsync(status, b->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream)) ||
         (e = cudaStreamSynchronize(b->stream)))
         return cuda_fail(ctx, e, "batch run");
-    if (status != 0) return set_error(ctx, CETRA_ETIMEOUT, "batch_run: a device wait timed out");
+    if (status[0] || status[1]) return set_error(ctx, CETRA_ETIMEOUT, "batch_run: a device wait timed out");
     return CETRA_OK;
 }
 
@@ -495,15 +494,15 @@ int cetra_batch_run_items(cetra_ctx *ctx, cetra_batch *b, const int64_t *items, 
                             cudaMemcpyHostToDevice, b->stream);
     if (!e && linear) e = enqueue_linear(b, b->lin_threads);
     if (!e) e = enqueue_fold(b, n_items, b->fold_variant, b->d_items);
-    int status = 0;
+    int status[2] = {0, 0};  // fold, linear stage
     if (!e && best)
         e = cudaMemcpyAsync(best, b->d_best, (size_t)b->n_curves * sizeof(cetra_best),
                             cudaMemcpyDeviceToHost, b->stream);
-    if (!e) e = cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaMemcpyAsync(status, b->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (!e) e = cudaStreamSynchronize(b->stream);
     if (e) return cuda_fail(ctx, e, "batch_run_items");
     ctx->launches += linear ? 4 : 2;
-    if (status != 0) return set_error(ctx, CETRA_ETIMEOUT, "batch_run_items: a device wait timed out");
+    if (status[0] || status[1]) return set_error(ctx, CETRA_ETIMEOUT, "batch_run_items: a device wait timed out");
     return CETRA_OK;
 }
 
@@ -527,12 +526,12 @@ int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *b, const float *d_scor
                                 b->d_counts);
     if (!e) e = enqueue_fold(b, b->n_items, b->fold_variant, b->d_items, b->d_counts);
     unsigned long long counts[2] = {0, 0};
-    int status = 0;
+    int status[2] = {0, 0};  // fold, linear stage
     if (!e && best)
         e = cudaMemcpyAsync(best, b->d_best, (size_t)b->n_curves * sizeof(cetra_best),
                             cudaMemcpyDeviceToHost, b->stream);
     if (!e) e = cudaMemcpyAsync(counts, b->d_counts, sizeof(counts), cudaMemcpyDeviceToHost, b->stream);
-    if (!e) e = cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaMemcpyAsync(status, b->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (!e) e = cudaStreamSynchronize(b->stream);
     if (!e && items_out && counts[0])
         e = cudaMemcpy(items_out, b->d_items, (size_t)counts[0] * sizeof(int64_t),
@@ -541,7 +540,7 @@ int cetra_batch_run_proposed(cetra_ctx *ctx, cetra_batch *b, const float *d_scor
     ctx->launches += linear ? 5 : 3;
     if (n_items_out) *n_items_out = (int64_t)counts[0];
     if (n_periods_out) *n_periods_out = (int64_t)counts[1];
-    if (status != 0)
+    if (status[0] || status[1])
         return set_error(ctx, CETRA_ETIMEOUT, "batch_run_proposed: a device wait timed out");
     return CETRA_OK;
 }

@@ -54,7 +54,8 @@ int cuda_fail(cetra_ctx *ctx, cudaError_t e, const char *what) {
 
 // The three device regions of a workspace.
 struct ws_ptrs {
-    float *wy, *w;
+    float2 *grid;  // interleaved (W y, W)
+    int *lin_status;
     float2 *ab;
     unsigned long long *keys;
     double *logl0;
@@ -63,7 +64,7 @@ struct ws_ptrs {
 
 ws_ptrs carve(void *base, const ws_layout &L) {
     char *b = static_cast<char *>(base);
-    return ws_ptrs{reinterpret_cast<float *>(b + L.wy), reinterpret_cast<float *>(b + L.w),
+    return ws_ptrs{reinterpret_cast<float2 *>(b + L.grid), reinterpret_cast<int *>(b + L.lin_status),
                    reinterpret_cast<float2 *>(b + L.ab),
                    reinterpret_cast<unsigned long long *>(b + L.keys),
                    reinterpret_cast<double *>(b + L.logl0), reinterpret_cast<int *>(b + L.status)};
@@ -251,9 +252,9 @@ int cetra_resample_device(cetra_ctx *ctx, const cetra_plan *plan, const double *
     if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "resample: workspace too small");
     device_guard g(ctx->device);
     ws_ptrs w = carve(d_workspace, L);
-    cudaError_t e = cudaMemsetAsync(w.wy, 0, L.ab - L.wy, ctx->stream);
+    cudaError_t e = cudaMemsetAsync(w.grid, 0, L.ab - L.grid, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "resample memset");
-    e = launch_resample(ctx, plan, d_time, d_flux, d_flux_err, n_points, w.wy, w.w);
+    e = launch_resample(ctx, plan, d_time, d_flux, d_flux_err, n_points, w.grid);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "resample launch");
     return CETRA_OK;
 }
@@ -272,7 +273,9 @@ int cetra_linear_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspac
                                       (size_t)(plan->ab_ld - plan->n_t0) * sizeof(float2),
                                       (size_t)plan->J, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "linear padding memset");
-    e = launch_linear(ctx, plan, w.wy, w.w, w.ab, d_depth, d_depth_var, d_dlogl);
+    e = cudaMemsetAsync(w.lin_status, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "linear status memset");
+    e = launch_linear(ctx, plan, w.grid, w.ab, d_depth, d_depth_var, d_dlogl, w.lin_status);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "linear launch");
     return CETRA_OK;
 }
@@ -307,12 +310,15 @@ int cetra_workspace_status(cetra_ctx *ctx, const cetra_plan *plan, const void *d
     ws_layout L = workspace_layout(plan, 0);
     if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "workspace_status: workspace too small");
     device_guard g(ctx->device);
-    int v = 0;
+    int v = 0, vl = 0;
     cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(d_workspace) + L.status,
                                     sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&vl, static_cast<const char *>(d_workspace) + L.lin_status,
+                            sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace_status");
-    *status = v;
+    *status = v ? v : vl;  // the periodic stage's word, else the linear stage's
     return CETRA_OK;
 }
 
@@ -324,7 +330,7 @@ int cetra_logl0_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_workspace
     if (workspace_bytes < L.total) return set_error(ctx, CETRA_ECAPACITY, "logl0: workspace too small");
     device_guard g(ctx->device);
     ws_ptrs w = carve(d_workspace, L);
-    cudaError_t e = launch_logl0(ctx, plan, w.wy, w.w, d_logl0);
+    cudaError_t e = launch_logl0(ctx, plan, w.grid, d_logl0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "logl0 launch");
     return CETRA_OK;
 }
@@ -587,7 +593,7 @@ int cetra_mask_transits_device(cetra_ctx *ctx, const cetra_plan *plan, void *d_w
     if (half_width == 0.0) return CETRA_OK;
     device_guard g(ctx->device);
     ws_ptrs w = carve(d_workspace, L);
-    cudaError_t e = launch_mask(ctx, plan, w.wy, w.w, period, t0, half_width, d_n_masked);
+    cudaError_t e = launch_mask(ctx, plan, w.grid, period, t0, half_width, d_n_masked);
     return e != cudaSuccess ? cuda_fail(ctx, e, "mask launch") : CETRA_OK;
 }
 

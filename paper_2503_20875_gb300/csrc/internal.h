@@ -150,7 +150,7 @@ double batch_period_host(double pmin, double ratio, int64_t k);
 
 // Workspace layout (byte offsets, 256-aligned).
 struct ws_layout {
-    size_t wy, w, ab, keys, logl0, status, total;
+    size_t grid, lin_status, ab, keys, logl0, status, total;
 };
 ws_layout workspace_layout(const cetra_plan *plan, int n_periods);
 
@@ -162,10 +162,18 @@ int plan_upload(cetra_ctx *ctx, cetra_plan *plan);
 void plan_free_device(cetra_plan *plan);
 
 // Kernel launchers (kernels.cu). Return cudaSuccess or the launch error.
+// The resampled grid is one interleaved (W y, W) pair per cell.
 cudaError_t launch_resample(cetra_ctx *ctx, const cetra_plan *plan, const double *time,
-                            const float *flux, const float *err, int64_t n, float *wy, float *w);
-cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
-                          float2 *ab, float *depth, float *var, float *dlogl);
+                            const float *flux, const float *err, int64_t n, float2 *grid);
+// status: set to CETRA_ETIMEOUT if a staging copy's bounded wait gave up (outputs NaN).
+cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float2 *grid, float2 *ab,
+                          float *depth, float *var, float *dlogl, int *status);
+// Dynamic shared memory of the linear kernel: the table chunk and the grid span, each with
+// two spare cells (a one-cell shift lines global 16-byte units up with shared ones).
+inline size_t linear_smem_bytes(int p, int threads, int kc) {
+    return ((size_t)((kc + 3) & ~1) + (size_t)p * threads * LIN_RB + (size_t)kc + 2) *
+           sizeof(float) * 2;
+}
 cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,
                         const double *periods, int K, const uint8_t *mask,
                         unsigned long long *keys, int *status);
@@ -173,7 +181,7 @@ cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2
                             const double *periods, int K, const unsigned long long *keys,
                             const int *status, double *dlogl, double *t0, double *dur, double *depth, double *var,
                             int64_t *oi, int32_t *oj);
-cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
+cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float2 *grid,
                          double *out);
 cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx);
 
@@ -181,11 +189,11 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx);
 cudaError_t launch_batch_resample(cudaStream_t stream, int num_sms, const cetra_plan *plan,
                                   const double *time, const float *flux, const float *err,
                                   int64_t n_points, const int64_t *pt_offsets, int n_curves,
-                                  const batch_curve *curves, float *wy, float *w);
+                                  const batch_curve *curves, float2 *grid);
 cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int threads,
                                 const int64_t *tile_off, int n_curves, int64_t n_tiles,
-                                const batch_curve *curves, const float *wy, const float *w,
-                                float2 *ab);
+                                const batch_curve *curves, const float2 *grid, float2 *ab,
+                                int *status);
 cudaError_t launch_batch_fold(cudaStream_t stream, int blocks, int variant, const cetra_plan *plan,
                               const float2 *ab, const batch_curve *curves,
                               const int64_t *group_off, int n_curves, int64_t n_items,
@@ -204,7 +212,7 @@ int peak_grid(int num_sms, bool smem);
 cudaError_t launch_peak(cudaStream_t stream, bool smem, int blocks, int iters, float *d_out,
                         double *work);
 // Method neighbours (neighbours.cu): masking a detected signal, single-transit events.
-cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float *wy, float *w, double P,
+cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float2 *grid, double P,
                         double t0, double h, unsigned long long *counts);
 size_t mono_scratch_words(const cetra_plan *plan, int max_events);
 cudaError_t launch_monotransits(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab,

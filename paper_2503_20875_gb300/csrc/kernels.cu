@@ -28,7 +28,7 @@ namespace {
 __global__ void resample_kernel(const double *__restrict__ time, const float *__restrict__ flux,
                                 const float *__restrict__ err, int64_t n, double t_ref, double c,
                                 int64_t n_pad, int64_t n_grid, int flux_is_offset,
-                                float *__restrict__ wy, float *__restrict__ w) {
+                                float2 *__restrict__ grid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         const double tk = time[k];
@@ -40,8 +40,7 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
         const int64_t bin = n_pad + (int64_t)v;
         const float wk = 1.0f / (ek * ek);
         const float yk = flux_is_offset ? fk : 1.0f - fk;
-        atomicAdd(&wy[bin], wk * yk);
-        atomicAdd(&w[bin], wk);
+        atomicAdd(&grid[bin], make_float2(wk * yk, wk));  // (W y, W), one cell
     }
 }
 
@@ -50,35 +49,71 @@ __global__ void resample_kernel(const double *__restrict__ time, const float *__
 // consecutive outputs u of that class); t0 index i = r + q u. For class r the window
 // of output u is grid points a + p u + k, k < len, with template samples tab[k]
 // (tables built on the host in FP64). The block stages a chunk of the table and the
-// matching span of the (W y, W) grid in shared memory; each thread slides a register
-// window over the span and accumulates RB outputs (A, B) with packed FP32x2 FMAs.
-// For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
+// matching span of the interleaved (W y, W) grid in shared memory with 1-D bulk copies (TMA);
+// each thread slides a register window over the span and accumulates RB outputs (A, B) with
+// packed FP32x2 FMAs. For p > 1 the span is read as p interleaved streams (k = p k1 + k2).
 // KAHAN: every term is added with Kahan compensation (CETRA_FP32_KAHAN).
-constexpr int LIN_STAGE_U = 4;  // staging loads in flight per thread (linear kernel)
+
+// Stage cells [x0, x0 + n) of a global array whose cells [0, nvalid) hold data into
+// dst[0 .. n) (cells outside [0, nvalid) read as zero). dst must sit at a byte address that is
+// 8 (x0 & 1) modulo 16, so that global cell pairs map to 16-byte units. The 16-byte aligned
+// interior of the valid range goes by one bulk copy that thread 0 issues on `bar` (after
+// `expect` was armed with the bytes of every copy of the chunk); the block's threads store
+// the at most two odd edge cells and the zero cells, which the copy never writes. Returns
+// the bytes of the bulk copy; `issue` = false only computes them.
+__device__ __forceinline__ uint32_t stage_cells(float2 *dst, const float2 *__restrict__ src,
+                                                int64_t x0, int n, int64_t nvalid, uint64_t *bar,
+                                                bool issue) {
+    const int64_t lo = x0 > 0 ? x0 : 0;
+    const int64_t hi = x0 + n < nvalid ? x0 + n : nvalid;
+    int64_t cs = (lo + 1) & ~(int64_t)1, ce = hi & ~(int64_t)1;
+    if (ce < cs) ce = cs;
+    const uint32_t bytes = hi > lo ? (uint32_t)(ce - cs) * (uint32_t)sizeof(float2) : 0u;
+    if (!issue) return bytes;
+    if (threadIdx.x == 0 && bytes) bulk_load(dst + (cs - x0), src + cs, bytes, bar);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int64_t x = x0 + k;
+        if (x >= lo && x < hi) {
+            if (bytes && x >= cs && x < ce) continue;  // the bulk copy's cells
+            dst[k] = src[x];
+        } else {
+            dst[k] = make_float2(0.f, 0.f);
+        }
+    }
+    return bytes;
+}
+
 template <int RB, bool KAHAN, int PFIX>
-__device__ __forceinline__ void linear_block(int tile, int jr, const float *__restrict__ wy,
-              const float *__restrict__ w, int64_t n_grid,
-              const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
+__device__ __forceinline__ void linear_block(int tile, int jr, const float2 *__restrict__ grid,
+              int64_t n_grid, const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
               const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off,
-              int p_arg, int q, int64_t I, int64_t ld, int kc_max, float2 *__restrict__ ab,
-              float *__restrict__ depth,
-              float *__restrict__ var, float *__restrict__ dlogl) {
+              int64_t n_table, int p_arg, int q, int64_t I, int64_t ld, int kc_max,
+              float2 *__restrict__ ab, float *__restrict__ depth, float *__restrict__ var,
+              float *__restrict__ dlogl, int *__restrict__ status) {
     // PFIX = 1: the t0 step equals the cadence (p = 1, the common case), known at compile time
     // so that the inner loop's shared-memory offsets are immediates
     const int p = PFIX ? PFIX : p_arg;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(128) float2 smem[];
+    __shared__ uint64_t bar;
     const int nthr = blockDim.x;
     const int t = threadIdx.x;
     const int j = jr / q, r = jr % q;
     const int64_t U = (r < I) ? (I - r + q - 1) / q : 0;
     const int64_t UT = (int64_t)nthr * RB;
     const int64_t u0 = (int64_t)tile * UT;
-    if (u0 >= U) return;
+    if (u0 >= U) return;  // uniform over the block
     const int padlen = win_padlen[jr];
     const int64_t a0 = (int64_t)win_a[jr] + (int64_t)p * u0;
-    const float2 *tab = tables + win_off[jr];
-    float2 *st = smem;           // [kc_max] template chunk (m, m^2)
-    float2 *sd = smem + kc_max;  // [p*UT + kc_max] grid span (W y, W)
+    const int64_t toff = win_off[jr];
+    // [kc_max + 2] template chunk (m, m^2), then [p UT + kc_max + 2] grid span (W y, W); each
+    // shifted by one cell when its first global cell is odd (16-byte units line up)
+    float2 *st_base = smem;
+    float2 *sd_base = smem + ((kc_max + 3) & ~1);
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
 
     // Blocked summation: `acc` collects at most LIN_SUB * RB terms before it is
     // folded into `tot`, so the FP32 rounding error grows with the block length
@@ -88,36 +123,31 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float *__re
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) acc[rr] = tot[rr] = make_float2(0.f, 0.f);
 
+    bool failed = false;
+    uint32_t phase = 0;
     for (int kc0 = 0; kc0 < padlen; kc0 += kc_max) {
         const int kcl = min(kc_max, padlen - kc0);
-        __syncthreads();
-        // staging: LIN_STAGE_U cells per thread in flight before the shared stores
-        for (int idx0 = t; idx0 < kcl; idx0 += LIN_STAGE_U * nthr) {
-            float2 v[LIN_STAGE_U];
-#pragma unroll
-            for (int u = 0; u < LIN_STAGE_U; ++u) {
-                const int idx = idx0 + u * nthr;
-                v[u] = idx < kcl ? tab[kc0 + idx] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < LIN_STAGE_U; ++u)
-                if (idx0 + u * nthr < kcl) st[idx0 + u * nthr] = v[u];
-        }
+        __syncthreads();  // the previous chunk is read
+        const int64_t tx0 = toff + kc0;
         const int64_t base = a0 + kc0;
         const int dl = (int)(p * UT) + kcl;
-        for (int idx0 = t; idx0 < dl; idx0 += LIN_STAGE_U * nthr) {
-            float2 v[LIN_STAGE_U];
-#pragma unroll
-            for (int u = 0; u < LIN_STAGE_U; ++u) {
-                const int64_t n = base + idx0 + u * nthr;
-                v[u] = make_float2(0.f, 0.f);
-                if (idx0 + u * nthr < dl && n >= 0 && n < n_grid) v[u] = make_float2(wy[n], w[n]);
-            }
-#pragma unroll
-            for (int u = 0; u < LIN_STAGE_U; ++u)
-                if (idx0 + u * nthr < dl) sd[idx0 + u * nthr] = v[u];
+        float2 *st = st_base + (tx0 & 1);
+        float2 *sd = sd_base + (base & 1);
+        if (t == 0) {
+            const uint32_t bytes = stage_cells(st, tables, tx0, kcl, n_table, &bar, false) +
+                                   stage_cells(sd, grid, base, dl, n_grid, &bar, false);
+            fence_proxy_async();
+            mbar_expect_tx(&bar, bytes);
         }
-        __syncthreads();
+        __syncthreads();  // armed before any copy can complete
+        stage_cells(st, tables, tx0, kcl, n_table, &bar, true);
+        stage_cells(sd, grid, base, dl, n_grid, &bar, true);
+        const bool ok = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {  // a copy did not land in time: stop (outputs NaN)
+            failed = true;
+            break;
+        }
         const int nk1 = kcl / p;  // a multiple of RB (tables are padded to p*RB)
         for (int k2 = 0; k2 < p; ++k2) {
             const float2 *V = sd + (int64_t)p * t * RB + k2;  // V[p m]: m-th sample of stream k2
@@ -152,6 +182,17 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float *__re
             }
         }
     }
+    if (failed) {
+        // wait (bounded) for the copy that did not land, so that it cannot land after the
+        // block exits; record the time-out; every output of the tile is NaN
+        if (t == 0) {
+            mbar_wait(&bar, phase ^ 1u);
+            atomicExch(status, CETRA_ETIMEOUT);
+        }
+        const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) tot[rr] = acc[rr] = make_float2(nan, nan);
+    }
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
         if constexpr (KAHAN)
@@ -168,31 +209,32 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float *__re
         const int64_t idx = (int64_t)j * I + i;
         const float A = acc[rr].x, B = acc[rr].y;
         ab[(int64_t)j * ld + i] = acc[rr];
-        const bool ok = B > 0.0f;
-        if (depth) depth[idx] = ok ? A / B : __int_as_float(0x7fc00000);
-        if (var) var[idx] = ok ? 1.0f / B : __int_as_float(0x7fc00000);
-        if (dlogl) dlogl[idx] = ok ? 0.5f * (A * (A / B)) : __int_as_float(0x7fc00000);
+        const bool good = B > 0.0f;
+        if (depth) depth[idx] = good ? A / B : __int_as_float(0x7fc00000);
+        if (var) var[idx] = good ? 1.0f / B : __int_as_float(0x7fc00000);
+        if (dlogl) dlogl[idx] = good ? 0.5f * (A * (A / B)) : __int_as_float(0x7fc00000);
     }
 }
 
 template <int RB, bool KAHAN>
 __global__ void __launch_bounds__(128, 4)
-linear_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n_grid,
+linear_kernel(const float2 *__restrict__ grid, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
-              const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off, int p,
-              int q, int64_t I, int64_t ld, int kc_max, const int32_t *__restrict__ order,
-              float2 *__restrict__ ab, float *__restrict__ depth, float *__restrict__ var,
-              float *__restrict__ dlogl) {
+              const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off,
+              int64_t n_table, int p, int q, int64_t I, int64_t ld, int kc_max,
+              const int32_t *__restrict__ order, float2 *__restrict__ ab,
+              float *__restrict__ depth, float *__restrict__ var, float *__restrict__ dlogl,
+              int *__restrict__ status) {
     // rows by decreasing window length: blocks are dispatched in y-major order, so the
     // longest blocks start first and the last wave holds the shortest ones
     if (p == 1)
-        linear_block<RB, KAHAN, 1>(blockIdx.x, order[blockIdx.y], wy, w, n_grid, tables, win_a,
-                                   win_padlen, win_off, p, q, I, ld, kc_max, ab, depth, var,
-                                   dlogl);
+        linear_block<RB, KAHAN, 1>(blockIdx.x, order[blockIdx.y], grid, n_grid, tables, win_a,
+                                   win_padlen, win_off, n_table, p, q, I, ld, kc_max, ab, depth,
+                                   var, dlogl, status);
     else
-        linear_block<RB, KAHAN, 0>(blockIdx.x, order[blockIdx.y], wy, w, n_grid, tables, win_a,
-                                   win_padlen, win_off, p, q, I, ld, kc_max, ab, depth, var,
-                                   dlogl);
+        linear_block<RB, KAHAN, 0>(blockIdx.x, order[blockIdx.y], grid, n_grid, tables, win_a,
+                                   win_padlen, win_off, n_table, p, q, I, ld, kc_max, ab, depth,
+                                   var, dlogl, status);
 }
 
 
@@ -245,15 +287,15 @@ __global__ void finalize_kernel(const float2 *__restrict__ ab, int64_t I, int64_
 // --------------------------------------------------------------------------------------------
 // Sec. 2.2 (last paragraph): logL0 = sum over non-null grid points of
 // -1/2 y^2 W - 1/2 ln(2 pi / W), y = (W y) / W, accumulated in FP64.
-__global__ void logl0_kernel(const float *__restrict__ wy, const float *__restrict__ w, int64_t n,
-                             double *out) {
+__global__ void logl0_kernel(const float2 *__restrict__ grid, int64_t n, double *out) {
     __shared__ double red[32];
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const double W = (double)w[k];
+        const float2 cell = grid[k];
+        const double W = (double)cell.y;
         if (!(W > 0.0)) continue;
-        const double y = (double)wy[k] / W;
+        const double y = (double)cell.x / W;
         acc += -0.5 * y * y * W - 0.5 * log(6.283185307179586 / W);
     }
 #pragma unroll
@@ -280,8 +322,8 @@ __global__ void batch_resample_kernel(const double *__restrict__ time,
                                       const float *__restrict__ err, int64_t n,
                                       const int64_t *__restrict__ pt_off, int n_curves,
                                       const batch_curve *__restrict__ curves, double c,
-                                      int64_t n_pad, int flux_is_offset, float *__restrict__ wy,
-                                      float *__restrict__ w) {
+                                      int64_t n_pad, int flux_is_offset,
+                                      float2 *__restrict__ grid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         const double tk = time[k];
@@ -293,8 +335,7 @@ __global__ void batch_resample_kernel(const double *__restrict__ time,
         const int64_t bin = cv.grid_off + n_pad + (int64_t)v;
         const float wk = 1.0f / (ek * ek);
         const float yk = flux_is_offset ? fk : 1.0f - fk;
-        atomicAdd(&wy[bin], wk * yk);
-        atomicAdd(&w[bin], wk);
+        atomicAdd(&grid[bin], make_float2(wk * yk, wk));
     }
 }
 
@@ -302,24 +343,24 @@ __global__ void batch_resample_kernel(const double *__restrict__ time,
 template <int RB, bool KAHAN>
 __global__ void __launch_bounds__(128, 4)
 batch_linear_kernel(const int64_t *__restrict__ tile_off, int n_curves,
-                    const batch_curve *__restrict__ curves, const float *__restrict__ wy,
-                    const float *__restrict__ w, const float2 *__restrict__ tables,
-                    const int32_t *__restrict__ win_a, const int32_t *__restrict__ win_padlen,
-                    const int64_t *__restrict__ win_off, int p, int q, int kc_max,
-                    const int32_t *__restrict__ order, float2 *__restrict__ ab) {
+                    const batch_curve *__restrict__ curves, const float2 *__restrict__ grid,
+                    const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
+                    const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off,
+                    int64_t n_table, int p, int q, int kc_max, const int32_t *__restrict__ order,
+                    float2 *__restrict__ ab, int *__restrict__ status) {
     const int cidx = csr_find(tile_off, n_curves, blockIdx.x);
     const batch_curve cv = curves[cidx];
     if (cv.I <= 0) return;
     if (p == 1)
         linear_block<RB, KAHAN, 1>((int)(blockIdx.x - tile_off[cidx]), order[blockIdx.y],
-                                   wy + cv.grid_off, w + cv.grid_off, cv.n_grid, tables, win_a,
-                                   win_padlen, win_off, p, q, cv.I, cv.ld, kc_max,
-                                   ab + cv.ab_off, nullptr, nullptr, nullptr);
+                                   grid + cv.grid_off, cv.n_grid, tables, win_a, win_padlen,
+                                   win_off, n_table, p, q, cv.I, cv.ld, kc_max, ab + cv.ab_off,
+                                   nullptr, nullptr, nullptr, status);
     else
         linear_block<RB, KAHAN, 0>((int)(blockIdx.x - tile_off[cidx]), order[blockIdx.y],
-                                   wy + cv.grid_off, w + cv.grid_off, cv.n_grid, tables, win_a,
-                                   win_padlen, win_off, p, q, cv.I, cv.ld, kc_max,
-                                   ab + cv.ab_off, nullptr, nullptr, nullptr);
+                                   grid + cv.grid_off, cv.n_grid, tables, win_a, win_padlen,
+                                   win_off, n_table, p, q, cv.I, cv.ld, kc_max, ab + cv.ab_off,
+                                   nullptr, nullptr, nullptr, status);
 }
 
 // The winner of every curve: its best period from the curve key, that period's best
@@ -579,7 +620,7 @@ __global__ void wait_timeout_selftest_kernel(int *out, int *status) {
 // launchers
 
 cudaError_t launch_resample(cetra_ctx *ctx, const cetra_plan *plan, const double *time,
-                            const float *flux, const float *err, int64_t n, float *wy, float *w) {
+                            const float *flux, const float *err, int64_t n, float2 *grid) {
     if (n <= 0) return cudaSuccess;
     const int threads = 256;
     int64_t blocks = (n + threads - 1) / threads;
@@ -587,7 +628,7 @@ cudaError_t launch_resample(cetra_ctx *ctx, const cetra_plan *plan, const double
     prof_mark(ctx, KID_RESAMPLE, true);
     resample_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(
         time, flux, err, n, plan->t_ref, plan->cadence, plan->n_pad, plan->n_grid,
-        plan->flux_is_offset, wy, w);
+        plan->flux_is_offset, grid);
     prof_mark(ctx, KID_RESAMPLE, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -601,7 +642,7 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
     if (kc < unit) kc = unit;
     if (plan->max_padlen > 0 && kc > plan->max_padlen) kc = plan->max_padlen;
     int threads = 128;
-    auto bytes = [&](int th, int k) { return ((size_t)p * th * LIN_RB + 2 * (size_t)k) * sizeof(float2); };
+    auto bytes = [&](int th, int k) { return linear_smem_bytes(p, th, k); };
     while (threads > 32 && bytes(threads, kc) > budget) threads /= 2;
     while (kc > unit && bytes(threads, kc) > budget) kc -= unit;
     plan->lin_threads = threads;
@@ -617,21 +658,21 @@ cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
     return fold_configure();
 }
 
-cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
-                          float2 *ab, float *depth, float *var, float *dlogl) {
+cudaError_t launch_linear(cetra_ctx *ctx, const cetra_plan *plan, const float2 *grid, float2 *ab,
+                          float *depth, float *var, float *dlogl, int *status) {
     const int64_t I = plan->n_t0, q = plan->q;
     const int64_t Umax = (I + q - 1) / q;
     const int64_t UT = (int64_t)plan->lin_threads * LIN_RB;
     const int64_t gx = (Umax + UT - 1) / UT;
     if (gx == 0) return cudaSuccess;
-    dim3 grid((unsigned)gx, (unsigned)(plan->J * q));
+    dim3 blocks((unsigned)gx, (unsigned)(plan->J * q));
     prof_mark(ctx, KID_LINEAR, true);
     auto kern = plan->precision == CETRA_FP32_KAHAN ? linear_kernel<LIN_RB, true>
                                                     : linear_kernel<LIN_RB, false>;
-    kern<<<grid, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
-        wy, w, plan->n_grid, plan->d_tables, plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
-        (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc, plan->d_lin_order, ab, depth, var,
-        dlogl);
+    kern<<<blocks, plan->lin_threads, plan->lin_smem, ctx->stream>>>(
+        grid, plan->n_grid, plan->d_tables, plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
+        (int64_t)plan->tables.size(), (int)plan->p, (int)q, I, plan->ab_ld, plan->lin_kc,
+        plan->d_lin_order, ab, depth, var, dlogl, status);
     prof_mark(ctx, KID_LINEAR, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -653,7 +694,7 @@ cudaError_t launch_finalize(cetra_ctx *ctx, const cetra_plan *plan, const float2
     return cudaGetLastError();
 }
 
-cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy, const float *w,
+cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float2 *grid,
                          double *out) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), ctx->stream);
     if (e != cudaSuccess) return e;
@@ -662,7 +703,7 @@ cudaError_t launch_logl0(cetra_ctx *ctx, const cetra_plan *plan, const float *wy
     if (blocks > (int64_t)ctx->num_sms * 4) blocks = (int64_t)ctx->num_sms * 4;
     if (blocks < 1) blocks = 1;
     prof_mark(ctx, KID_LOGL0, true);
-    logl0_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(wy, w, plan->n_grid, out);
+    logl0_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(grid, plan->n_grid, out);
     prof_mark(ctx, KID_LOGL0, false);
     ctx->launches++;
     return cudaGetLastError();
@@ -683,32 +724,32 @@ double batch_period_host(double pmin, double ratio, int64_t k) {
 cudaError_t launch_batch_resample(cudaStream_t stream, int num_sms, const cetra_plan *plan,
                                   const double *time, const float *flux, const float *err,
                                   int64_t n_points, const int64_t *pt_offsets, int n_curves,
-                                  const batch_curve *curves, float *wy, float *w) {
+                                  const batch_curve *curves, float2 *grid) {
     if (n_points <= 0) return cudaSuccess;
     const int threads = 256;
     int64_t blocks = (n_points + threads - 1) / threads;
     if (blocks > (int64_t)num_sms * 32) blocks = (int64_t)num_sms * 32;
     batch_resample_kernel<<<(unsigned)blocks, threads, 0, stream>>>(
         time, flux, err, n_points, pt_offsets, n_curves, curves, plan->cadence, plan->n_pad,
-        plan->flux_is_offset, wy, w);
+        plan->flux_is_offset, grid);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_linear(cudaStream_t stream, const cetra_plan *plan, int threads,
                                 const int64_t *tile_off, int n_curves, int64_t n_tiles,
-                                const batch_curve *curves, const float *wy, const float *w,
-                                float2 *ab) {
+                                const batch_curve *curves, const float2 *grid, float2 *ab,
+                                int *status) {
     if (n_tiles <= 0) return cudaSuccess;
     if (n_tiles > 2147483647) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)n_tiles, (unsigned)(plan->J * plan->q));
-    const size_t smem = ((size_t)plan->p * threads * LIN_RB + 2 * (size_t)plan->lin_kc) *
-                        sizeof(float2);
+    dim3 blocks((unsigned)n_tiles, (unsigned)(plan->J * plan->q));
+    const size_t smem = linear_smem_bytes((int)plan->p, threads, plan->lin_kc);
     auto kern = plan->precision == CETRA_FP32_KAHAN ? batch_linear_kernel<LIN_RB, true>
                                                     : batch_linear_kernel<LIN_RB, false>;
-    kern<<<grid, threads, smem, stream>>>(tile_off, n_curves, curves, wy, w, plan->d_tables,
-                                          plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
-                                          (int)plan->p, (int)plan->q, plan->lin_kc,
-                                          plan->d_lin_order, ab);
+    kern<<<blocks, threads, smem, stream>>>(tile_off, n_curves, curves, grid, plan->d_tables,
+                                            plan->d_win_a, plan->d_win_padlen, plan->d_win_off,
+                                            (int64_t)plan->tables.size(), (int)plan->p,
+                                            (int)plan->q, plan->lin_kc, plan->d_lin_order, ab,
+                                            status);
     return cudaGetLastError();
 }
 
@@ -738,7 +779,7 @@ cudaError_t launch_batch_select(cudaStream_t stream, const batch_curve *curves,
 }
 
 cudaError_t batch_configure(const cetra_plan *plan) {
-    const size_t lin_max = ((size_t)plan->p * 128 * LIN_RB + 2 * (size_t)plan->lin_kc) * sizeof(float2);
+    const size_t lin_max = linear_smem_bytes((int)plan->p, 128, plan->lin_kc);
     for (auto fn : {batch_linear_kernel<LIN_RB, false>, batch_linear_kernel<LIN_RB, true>}) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)lin_max);

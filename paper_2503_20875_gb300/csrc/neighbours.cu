@@ -14,7 +14,7 @@ constexpr int NB_THREADS = 256;
 // Null cell k (W y = W = 0) when its time g = t_ref + (k - n_pad) c is within h of a mid-time
 // t0 + n P, n = floor((g - t0) / P + 1/2) the nearest epoch; FP64, one rounding per operation.
 // counts[0] += cells that held data (counts may be NULL).
-__global__ void mask_kernel(float *__restrict__ wy, float *__restrict__ w, int64_t n_grid,
+__global__ void mask_kernel(float2 *__restrict__ grid, int64_t n_grid,
                             double t_ref, double c, int64_t n_pad, double P, double t0, double h,
                             unsigned long long *__restrict__ counts) {
     unsigned long long mine = 0;
@@ -25,9 +25,8 @@ __global__ void mask_kernel(float *__restrict__ wy, float *__restrict__ w, int64
         const double n = floor(__dadd_rn(__ddiv_rn(d, P), 0.5));
         const double r = fabs(__dsub_rn(d, __dmul_rn(n, P)));
         if (r < h) {
-            mine += w[k] > 0.0f;
-            wy[k] = 0.0f;
-            w[k] = 0.0f;
+            mine += grid[k].y > 0.0f;
+            grid[k] = make_float2(0.0f, 0.0f);
         }
     }
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xFFFFFFFFu, mine, o);
@@ -119,10 +118,10 @@ unsigned blocks_for(int64_t n, int num_sms) {
 
 }  // namespace
 
-cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float *wy, float *w, double P,
+cudaError_t launch_mask(cetra_ctx *ctx, const cetra_plan *plan, float2 *grid, double P,
                         double t0, double h, unsigned long long *counts) {
     mask_kernel<<<blocks_for(plan->n_grid, ctx->num_sms), NB_THREADS, 0, ctx->stream>>>(
-        wy, w, plan->n_grid, plan->t_ref, plan->cadence, plan->n_pad, P, t0, h, counts);
+        grid, plan->n_grid, plan->t_ref, plan->cadence, plan->n_pad, P, t0, h, counts);
     ctx->launches++;
     return cudaGetLastError();
 }

@@ -266,10 +266,10 @@ ws_layout workspace_layout(const cetra_plan *plan, int n_periods) {
     ws_layout L{};
     size_t ng = (size_t)plan->n_grid;
     size_t off = 0;
-    L.wy = off;
-    off = up(off + ng * sizeof(float));
-    L.w = off;
-    off = up(off + ng * sizeof(float));
+    L.grid = off;  // interleaved (W y, W) per resampled cell
+    off = up(off + ng * sizeof(float2));
+    L.lin_status = off;  // bounded-wait status of the linear stage
+    off = up(off + sizeof(int));
     L.ab = off;
     off = up(off + (size_t)plan->J * (size_t)plan->ab_ld * sizeof(float2));
     L.logl0 = off;
