@@ -634,14 +634,21 @@ cudaError_t launch_resample(cetra_ctx *ctx, const cetra_plan *plan, const double
     return cudaGetLastError();
 }
 
+#ifndef LIN_THREADS
+#define LIN_THREADS 128  // threads per linear block (RB outputs each)
+#endif
+#ifndef LIN_KC
+#define LIN_KC 2304      // template samples per staged table chunk (before rounding to p RB)
+#endif
+
 cudaError_t linear_configure(cetra_plan *plan, const cetra_ctx *ctx) {
     const int p = (int)plan->p;
     const size_t budget = 100 * 1024;  // keeps two blocks resident per SM at the largest shape
     const int unit = p * LIN_RB;
-    int kc = (2304 / unit) * unit;
+    int kc = (LIN_KC / unit) * unit;
     if (kc < unit) kc = unit;
     if (plan->max_padlen > 0 && kc > plan->max_padlen) kc = plan->max_padlen;
-    int threads = 128;
+    int threads = LIN_THREADS;
     auto bytes = [&](int th, int k) { return linear_smem_bytes(p, th, k); };
     while (threads > 32 && bytes(threads, kc) > budget) threads /= 2;
     while (kc > unit && bytes(threads, kc) > budget) kc -= unit;
