@@ -718,7 +718,7 @@ def main():
     hbm_achieved = traffic / (fold_ms_per * 1e-3) / 1e9 if traffic else None
     hbm_frac = hbm_achieved / hbm_peak if traffic else None
     smem_frac = achieved / smem_peak
-    roofline = {"bound": "smem", "kernel": "fold_tma_kernel", "achieved": achieved,
+    roofline = {"bound": "smem", "kernel": "fold_kernel", "achieved": achieved,
                 "peak": smem_peak, "unit": "GB/s", "frac": smem_frac, "traffic": traffic,
                 "peak_source": f"{sm_count} SMs x 128 B/clk x {clk:.0f} MHz (shared-memory loads)",
                 "hbm_achieved": hbm_achieved, "hbm_peak": hbm_peak, "hbm_frac": hbm_frac,
