@@ -1080,7 +1080,11 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
     if (K <= 0) return cudaSuccess;
     const int n_groups = (K + FT_G - 1) / FT_G;
     const size_t grid_bytes = (size_t)plan->J * (size_t)plan->ab_ld * sizeof(float2);
-    const int jchunk = grid_bytes > FT_L2_GRID_BYTES ? 1 : plan->J;
+    // one duration per work item when the grid exceeds the L2 (the blocks in flight then share
+    // a row), or when whole groups would not give every block slot of the GPU four items
+    const int64_t slots = (int64_t)ctx->num_sms * FT_MIN_BLOCKS;
+    const int jchunk =
+        (grid_bytes > FT_L2_GRID_BYTES || (int64_t)n_groups < 4 * slots) ? 1 : plan->J;
     const int n_chunks = (plan->J + jchunk - 1) / jchunk;
     const int64_t items = (int64_t)n_groups * n_chunks;
     if (items > 2147483647) return cudaErrorInvalidConfiguration;

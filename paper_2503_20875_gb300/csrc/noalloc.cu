@@ -16,8 +16,10 @@
 // exits. All calls on one device share it: calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on it and must be
 // serialised by the caller. Each call clears the status word before its fold
-// runs. The keys are not cleared: every block of a fold that completes writes the
-// keys of all its periods before the finalize kernel reads them, and a block whose
+// runs. The keys are cleared only when the fold splits a period's durations over
+// several blocks (it then zeroes them and combines the blocks' keys by atomic max);
+// otherwise every block of a fold that completes writes the keys of all its
+// periods before the finalize kernel reads them, and in both cases a block whose
 // bounded wait gives up stops without writing its keys but first records
 // CETRA_ETIMEOUT in the status word. The finalize kernel reads the status word
 // first and writes NaN for every period when it is non-zero, so keys left over
