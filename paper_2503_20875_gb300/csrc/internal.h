@@ -90,7 +90,13 @@ struct cetra_linear_grid {
 
 // Register block of the linear kernel: outputs per thread. Odd, so that the
 // stride-RB shared-memory reads of a warp fall in distinct banks.
-constexpr int LIN_RB = 9;
+#ifndef LIN_RB_OUTPUTS
+#define LIN_RB_OUTPUTS 9
+#endif
+constexpr int LIN_RB = LIN_RB_OUTPUTS;
+#ifndef LIN_MIN_BLOCKS
+#define LIN_MIN_BLOCKS 4  // resident linear blocks per SM the register allocation must allow
+#endif
 constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear kernel
 // Fold kernel shape (fold.cu, compile-time). A block is FT_THREADS consumer threads, each
 // folding FT_R phases of every period of a group of up to FT_G periods, plus one producer warp

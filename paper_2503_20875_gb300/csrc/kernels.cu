@@ -71,16 +71,28 @@ __device__ __forceinline__ uint32_t stage_cells(float2 *dst, const float2 *__res
     const uint32_t bytes = hi > lo ? (uint32_t)(ce - cs) * (uint32_t)sizeof(float2) : 0u;
     if (!issue) return bytes;
     if (threadIdx.x == 0 && bytes) bulk_load(dst + (cs - x0), src + cs, bytes, bar);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int64_t x = x0 + k;
-        if (x >= lo && x < hi) {
-            if (bytes && x >= cs && x < ce) continue;  // the bulk copy's cells
-            dst[k] = src[x];
-        } else {
-            dst[k] = make_float2(0.f, 0.f);
-        }
-    }
+    // local ranges: zeros [0, v0) and [v1, n); plain copies [v0, c0) and [c1, v1)
+    const int v0 = hi > lo ? (int)(lo - x0) : n, v1 = hi > lo ? (int)(hi - x0) : n;
+    const int c0 = bytes ? (int)(cs - x0) : v1, c1 = bytes ? (int)(ce - x0) : v1;
+    for (int k = threadIdx.x; k < v0; k += blockDim.x) dst[k] = make_float2(0.f, 0.f);
+    for (int k = v1 + threadIdx.x; k < n; k += blockDim.x) dst[k] = make_float2(0.f, 0.f);
+    for (int k = v0 + threadIdx.x; k < c0; k += blockDim.x) dst[k] = src[x0 + k];
+    for (int k = c1 + threadIdx.x; k < v1; k += blockDim.x) dst[k] = src[x0 + k];
     return bytes;
+}
+
+// One window's outputs: (A, B) into the grid row j, and the three Sec. 2.2 outputs (depth
+// A/B, its variance 1/B, ΔlogL A²/(2B)) when requested; NaN where B = 0 (a null window).
+__device__ __forceinline__ void linear_store(float2 v, int64_t i, int j, int64_t I, int64_t ld,
+                                             float2 *__restrict__ ab, float *__restrict__ depth,
+                                             float *__restrict__ var, float *__restrict__ dlogl) {
+    const int64_t idx = (int64_t)j * I + i;
+    const float A = v.x, B = v.y;
+    ab[(int64_t)j * ld + i] = v;
+    const bool good = B > 0.0f;
+    if (depth) depth[idx] = good ? A / B : __int_as_float(0x7fc00000);
+    if (var) var[idx] = good ? 1.0f / B : __int_as_float(0x7fc00000);
+    if (dlogl) dlogl[idx] = good ? 0.5f * (A * (A / B)) : __int_as_float(0x7fc00000);
 }
 
 template <int RB, bool KAHAN, int PFIX>
@@ -184,14 +196,20 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float2 *__r
     }
     if (failed) {
         // wait (bounded) for the copy that did not land, so that it cannot land after the
-        // block exits; record the time-out; every output of the tile is NaN
+        // block exits; record the time-out; every output of the tile is NaN, written directly
+        // (the staging buffer may still receive that copy)
         if (t == 0) {
             mbar_wait(&bar, phase ^ 1u);
             atomicExch(status, CETRA_ETIMEOUT);
         }
         const float nan = __int_as_float(0x7fc00000);
-#pragma unroll
-        for (int rr = 0; rr < RB; ++rr) tot[rr] = acc[rr] = make_float2(nan, nan);
+        for (int rr = 0; rr < RB; ++rr) {
+            const int64_t u = u0 + (int64_t)t * RB + rr;
+            if (u >= U) break;
+            linear_store(make_float2(nan, nan), r + (int64_t)q * u, j, I, ld, ab, depth, var,
+                         dlogl);
+        }
+        return;
     }
 #pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
@@ -201,23 +219,21 @@ __device__ __forceinline__ void linear_block(int tile, int jr, const float2 *__r
             acc[rr] = tot[rr];
     }
 
+    // A thread holds RB consecutive t0 of the tile; a warp's direct stores would touch a
+    // separate 32-byte sector per lane. The sums go through shared memory (the staged chunk
+    // is no longer read) so that consecutive lanes store consecutive t0.
+    __syncthreads();
+    float2 *so = smem;  // UT cells: the dynamic buffer holds at least p UT + 2 kc_max + 4
 #pragma unroll
-    for (int rr = 0; rr < RB; ++rr) {
-        const int64_t u = u0 + (int64_t)t * RB + rr;
-        if (u >= U) break;
-        const int64_t i = r + (int64_t)q * u;
-        const int64_t idx = (int64_t)j * I + i;
-        const float A = acc[rr].x, B = acc[rr].y;
-        ab[(int64_t)j * ld + i] = acc[rr];
-        const bool good = B > 0.0f;
-        if (depth) depth[idx] = good ? A / B : __int_as_float(0x7fc00000);
-        if (var) var[idx] = good ? 1.0f / B : __int_as_float(0x7fc00000);
-        if (dlogl) dlogl[idx] = good ? 0.5f * (A * (A / B)) : __int_as_float(0x7fc00000);
-    }
+    for (int rr = 0; rr < RB; ++rr) so[t * RB + rr] = acc[rr];
+    __syncthreads();
+    const int nU = (int)min(UT, U - u0);
+    for (int k = t; k < nU; k += nthr)
+        linear_store(so[k], r + (int64_t)q * (u0 + k), j, I, ld, ab, depth, var, dlogl);
 }
 
 template <int RB, bool KAHAN>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, LIN_MIN_BLOCKS)
 linear_kernel(const float2 *__restrict__ grid, int64_t n_grid,
               const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
               const int32_t *__restrict__ win_padlen, const int64_t *__restrict__ win_off,
@@ -341,7 +357,7 @@ __global__ void batch_resample_kernel(const double *__restrict__ time,
 
 // Sec. 2.2 for every curve: x-blocks enumerate the t0 tiles of all curves.
 template <int RB, bool KAHAN>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, LIN_MIN_BLOCKS)
 batch_linear_kernel(const int64_t *__restrict__ tile_off, int n_curves,
                     const batch_curve *__restrict__ curves, const float2 *__restrict__ grid,
                     const float2 *__restrict__ tables, const int32_t *__restrict__ win_a,
