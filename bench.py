@@ -24,6 +24,10 @@ periods 0.5-13.5 d (synthetic, seeded).
          bounded sample (the whole linear search + the fold on every n-th
          period); ms_per_step is that sample's measured time, value the
          curves/s extrapolated from it (key extrapolated_ms_per_curve)
+  other_configs     (default run on one GPU) the 2-min 27-d curve, the compensated
+         form of the 20-s curve, the 4-yr 1-min curve and the batched form on 512
+         multi-sector curves, each measured by a child run of this script with its
+         own arguments (key args) and summarised from that run's JSON line
 
 Multi-GPU: one process per GPU (torchrun); each rank searches its own curves
 (replicas, no collective on the data path); value = all ranks' curves / max
@@ -84,6 +88,10 @@ def parse():
     ap.add_argument("--neighbours", action="store_true",
                     help="single-transit search of the 4-yr 1-min curve and the three-round "
                          "search-and-mask of the 20-s TESS curve")
+    ap.add_argument("--other-configs", choices=["auto", "off"], default="auto",
+                    help="auto: the default run (20-s curve, plain FP32, one GPU) also measures "
+                         "the other single-GPU configurations, each in a child process, and adds "
+                         "a summary of each one's line under other_configs")
     ap.add_argument("--period-range", default=None,
                     help="a:b, search only periods[a:b] of the workload (profiling a small case)")
     return ap.parse_args()
@@ -762,10 +770,62 @@ def main():
             "wall_s_timed": wall, "best_period_d": float(w.periods[best]) if best is not None and best >= 0 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_fold_stride)
+    if (rank == 0 and world == 1 and args.other_configs == "auto" and not args.period_range
+            and args.workload == "tess_20s_27d" and args.precision == "fp32"):
+        line["other_configs"] = other_configs()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# The other single-GPU configurations the default run also measures: (name, arguments).
+OTHER_CONFIGS = [
+    ("tess_2min_27d", ["--workload", "tess_2min_27d", "--steps", "20", "--warmup", "3"]),
+    ("tess_20s_27d kahan", ["--precision", "kahan", "--steps", "5", "--warmup", "3",
+                            "--no-cpu-baseline"]),
+    ("kepler_1min_4yr", ["--workload", "kepler_1min_4yr", "--steps", "3", "--warmup", "3",
+                         "--e2e-steps", "1", "--no-cpu-baseline"]),
+    ("batch_30min_512", ["--batch-curves", "512", "--steps", "2", "--warmup", "1"]),
+]
+
+
+def other_configs():
+    """Run each of OTHER_CONFIGS as a child bench process (one at a time, same GPU) and keep
+    the figures of its JSON line; a child that fails is recorded with its error."""
+    out = {}
+    for name, extra in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.abspath(__file__), *extra, "--other-configs", "off"]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception as e:  # noqa: BLE001 - recorded, the main line still prints
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            continue
+        keep = {k: d[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                  "gpu_launches") if k in d}
+        keep["args"] = " ".join(extra)
+        keep["config"] = {k: d["config"][k] for k in ("workload", "precision", "n_periods",
+                                                      "n_t0", "n_durations") if k in d["config"]}
+        if d.get("e2e"):
+            keep["e2e"] = {k: d["e2e"].get(k) for k in ("value", "unit", "api")}
+        if d.get("roofline"):
+            keep["roofline"] = {k: d["roofline"].get(k) for k in ("bound", "kernel", "achieved",
+                                                                 "peak", "unit", "frac",
+                                                                 "traffic", "hbm_frac")}
+        if d.get("roofline_linear"):
+            keep["roofline_linear"] = {k: d["roofline_linear"].get(k)
+                                       for k in ("achieved", "frac", "frac_of_measured")}
+        for k in ("clocks", "plain_form", "recovery"):
+            if k in d:
+                keep[k] = d[k]
+        if d.get("cpu_baseline"):
+            keep["cpu_baseline"] = {k: d["cpu_baseline"].get(k)
+                                    for k in ("value", "unit", "cores", "kind")}
+        keep["wall_s"] = time.perf_counter() - t0
+        out[name] = keep
+    return out
 
 
 def info_table_work(plan):

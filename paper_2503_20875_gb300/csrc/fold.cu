@@ -353,7 +353,47 @@ __device__ __forceinline__ bool consume_epochs(fold_smem &sm, const fold_table &
                                                unsigned use, uint32_t mine, uint64_t (&acc)[GS][R],
                                                uint64_t (&cmp)[KAHAN ? GS : 1][KAHAN ? R : 1],
                                                ring &rg) {
-    for (int e = 2; e < nE; ++e) {
+    int e = 2;
+    if constexpr (KAHAN) {
+        // The compensated form takes the epochs in groups of FT_KAHAN_GROUP (when the ring has
+        // that many stages): the group's cells are added plainly, and the group sum enters the
+        // compensated sum, so a cell costs 1 + 4 / FT_KAHAN_GROUP packed operations instead of
+        // 5 and the shared-memory loads stay the bound. Error: FT_KAHAN_GROUP - 1 roundings
+        // per group sum on top of the compensated sum's own bound.
+        constexpr int KG = FT_KAHAN_GROUP;
+        if (rg.ns >= (uint32_t)KG) {
+            for (; e + KG - 1 < nE; e += KG) {
+                uint32_t st[KG], ad[KG];
+#pragma unroll
+                for (int k = 0; k < KG; ++k) {
+                    if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
+                    st[k] = rg.stage;
+                    ad[k] = mine + rg.stage * rg.bytes;
+                    rg.next();
+                }
+                epoch_offsets<GS, W> off[KG];
+#pragma unroll
+                for (int k = 0; k < KG; ++k) off[k].load(tb.off + (uint32_t)((e + k) * GS * W));
+#pragma unroll
+                for (int gg = 0; gg < GS; ++gg) {
+                    if (!ALL && !((use >> gg) & 1u)) continue;
+                    uint64_t v[KG][R];
+#pragma unroll
+                    for (int k = 0; k < KG; ++k) lds_rows<0, R>(v[k], ad[k] + off[k][gg]);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        uint64_t g = v[0][r];
+#pragma unroll
+                        for (int k = 1; k < KG; ++k) g = sum_pair(g, v[k][r]);
+                        kahan_add_pair(acc[gg][r], cmp[gg][r], g);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < KG; ++k) mbar_arrive(&sm.empty[st[k]]);
+            }
+        }
+    }
+    for (; e < nE; ++e) {
         if (!fold_wait(sm, &sm.full[rg.stage], rg.parity())) return false;
         const uint32_t a = mine + rg.stage * rg.bytes;
         epoch_offsets<GS, W> off;

@@ -107,6 +107,9 @@ constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear ke
 #ifndef FT_STRIP
 #define FT_STRIP 2048     // cells per staged strip at most (a tile plus the offsets' spread)
 #endif
+#ifndef FT_KAHAN_GROUP
+#define FT_KAHAN_GROUP 2  // epochs summed plainly before each compensated step
+#endif
 #ifndef FT_NSTAGE
 #define FT_NSTAGE 8       // strips in flight per block at most (as many as the ring holds)
 #endif
