@@ -503,6 +503,7 @@ def run_proposal(args):
         sweep.append(point)
     head = next(x for x in sweep if x["top_frac"] == args.proposal_frac)
     equal = [x for x in sweep if x["recall"]["learned"] >= rec_full]
+    equal_lr = [x for x in sweep if x["recall"]["lr_only"] >= rec_full]
     split_l = dict(split_l, select_fold_ms=head["select_fold_ms"])
     line = {"metric": "learned proposal: light curves searched/s vs the full periodic search, "
                       "at injected-planet recall",
@@ -524,6 +525,11 @@ def run_proposal(args):
                               "speedup": equal[0]["speedup"]} if equal else
                              {"top_frac": None, "note": "no swept fraction recovers as many "
                               "injected planets as the full search"}),
+            # the same for the window-LR map alone (no network), the proposal's own baseline
+            "equal_recall_lr_only": ({"top_frac": equal_lr[0]["top_frac"],
+                                      "value": equal_lr[0]["lr_only_value"],
+                                      "speedup": equal_lr[0]["lr_only_value"] * t_full / n_eval}
+                                     if equal_lr else {"top_frac": None}),
             "train": {"curves": n_train, "with_planet": n_planets, "points": n_points,
                       "epochs": args.proposal_epochs, "loss": [round(h, 5) for h in hist],
                       "data_s": t_data, "data_split": split, "train_s": t_train,
