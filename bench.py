@@ -20,6 +20,9 @@ periods 0.5-13.5 d (synthetic, seeded).
   roofline_linear   the linear kernel's FP32 FMA rate against the FMA peak
          (both carry the library's own measured ceilings: peak_measured)
   cpu_baseline      the FP64 CPU oracle on a bounded sample of the step
+  accuracy          the timed run's own outputs against that oracle sample: the
+         linear ΔlogL at every window with LR >= 25, and the sampled periods'
+         winners (ΔlogL relative error, same (duration, t0) cell)
   --impl reference   the FP64 CPU oracle on the host cores: each step is one
          bounded sample (the whole linear search + the fold on every n-th
          period); ms_per_step is that sample's measured time, value the
@@ -197,9 +200,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(w, stride, durations=None):
+def cpu_baseline(w, stride, durations=None, keep=None):
     """The FP64 oracle on this host's cores: the whole linear search plus the
-    fold on every stride-th period, extrapolated to one full curve."""
+    fold on every stride-th period, extrapolated to one full curve. keep (a dict), when
+    given, receives the oracle's outputs (the linear LR grid, the sampled periods' results)."""
     import oracle
     oracle.build()
     d = w.durations if durations is None else durations
@@ -211,8 +215,10 @@ def cpu_baseline(w, stride, durations=None):
     t_lin = time.perf_counter() - t0
     sel = w.periods[::stride]
     t1 = time.perf_counter()
-    oracle.periodic(g, d, dep, var, lr, sel)
+    per = oracle.periodic(g, d, dep, var, lr, sel)
     t_fold = time.perf_counter() - t1
+    if keep is not None:
+        keep.update(lr=lr, periodic=per, stride=stride)
     per_curve = t_lin + t_fold * (w.periods.size / sel.size)
     return {"value": 1.0 / per_curve, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
@@ -775,7 +781,9 @@ def main():
             "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kern.items()},
             "wall_s_timed": wall, "best_period_d": float(w.periods[best]) if best is not None and best >= 0 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_fold_stride)
+        ref = {}
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_fold_stride, keep=ref)
+        line["accuracy"] = accuracy(ds, ref)
     if (rank == 0 and world == 1 and args.other_configs == "auto" and not args.period_range
             and args.workload == "tess_20s_27d" and args.precision == "fp32"):
         line["other_configs"] = other_configs()
@@ -783,6 +791,32 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def accuracy(ds, ref):
+    """The timed run's own outputs against the FP64 oracle of the cpu_baseline leg: the linear
+    ΔlogL at every window with LR >= 25, and each sampled period's winner (ΔlogL, and whether
+    its (duration, t0) cell is the oracle's)."""
+    stride = ref["stride"]
+    o_lr = ref["lr"]
+    g_lr = ds.dlogl.cpu().numpy().astype(np.float64) if ds.dlogl is not None else None
+    out = {"reference": "FP64 oracle (cpu_baseline leg)"}
+    if g_lr is not None:
+        sig = np.isfinite(o_lr) & (o_lr >= 25.0)
+        rel = np.abs(g_lr[sig] - o_lr[sig]) / np.abs(o_lr[sig])
+        out["linear"] = {"windows": int(sig.sum()), "max_rel_err_dlogl": float(rel.max()),
+                         "null_masks_equal": bool(np.array_equal(np.isnan(g_lr), np.isnan(o_lr)))}
+    o = ref["periodic"]
+    g = {k: v.cpu().numpy()[::stride] for k, v in ds.out.items()}
+    ok = np.isfinite(o["dlogl"]) & np.isfinite(g["dlogl"])
+    rel = np.abs(g["dlogl"][ok] - o["dlogl"][ok]) / np.maximum(np.abs(o["dlogl"][ok]), 1e-300)
+    same = (g["i"][ok] == o["i"][ok]) & (g["j"][ok] == o["j"][ok])
+    out["periodic"] = {"periods": int(o["dlogl"].size), "compared": int(ok.sum()),
+                       "max_rel_err_dlogl": float(rel.max()) if rel.size else None,
+                       "argmax_cell_equal": float(same.mean()) if same.size else None,
+                       "null_masks_equal": bool(np.array_equal(np.isnan(g["dlogl"]),
+                                                               np.isnan(o["dlogl"])))}
+    return out
 
 
 # The other single-GPU configurations the default run also measures: (name, arguments).
@@ -823,7 +857,7 @@ def other_configs():
         if d.get("roofline_linear"):
             keep["roofline_linear"] = {k: d["roofline_linear"].get(k)
                                        for k in ("achieved", "frac", "frac_of_measured")}
-        for k in ("clocks", "plain_form", "recovery"):
+        for k in ("clocks", "plain_form", "recovery", "accuracy"):
             if k in d:
                 keep[k] = d[k]
         if d.get("cpu_baseline"):
