@@ -56,7 +56,7 @@ UNIT = "curves/s"
 FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one full fold launch per workload (one ncu
 # capture of the current fold kernel; an entry is removed whenever the kernel changes)
-FOLD_DRAM_BYTES = {"tess_20s_27d": 20021248 + 118016, "kepler_1min_4yr": 526165504 + 9621504}
+FOLD_DRAM_BYTES = {"tess_20s_27d": 20452096 + 0, "kepler_1min_4yr": 527190528 + 9241600}
 
 
 def parse():

@@ -325,6 +325,20 @@ __device__ __forceinline__ int live_epochs(const fold_table &tb, int nE, int I, 
     return nE;
 }
 
+// Rows of a tile whose row has `rem` phases left (rem >= 1): the last tile of a row folds
+// only the rows of FT_THREADS phases that hold some phase of the sub-group, so its lanes past
+// the last phase neither copy nor load cells. (Sub-groups of fewer than 4 periods, which only
+// tables too large for 4 give, always fold R rows: fewer kernel variants.)
+template <int GS, int R>
+__device__ __forceinline__ int tile_rows(int rem) {
+    if constexpr (GS < 4 || R == 1) {
+        return R;
+    } else {
+        const int rows = (rem + FT_THREADS - 1) / FT_THREADS;
+        return rows < R ? rows : R;
+    }
+}
+
 // Run by the producer warp's first lane alone.
 template <int GS, int R>
 __device__ void produce_main(fold_smem &sm, uint32_t ring0, const fold_table &tb, int g0,
@@ -336,10 +350,11 @@ __device__ void produce_main(fold_smem &sm, uint32_t ring0, const fold_table &tb
         int nE = tb.Es;
         for (int i0 = 0; i0 < nph_sub; i0 += T) {
             nE = live_epochs(tb, nE, I, i0);
+            const int TL = FT_THREADS * tile_rows<GS, R>(nph_sub - i0);  // phases of this tile
             for (int e = 0; e < nE; ++e) {
                 if (!producer_wait(sm, &sm.empty[rg.stage], rg.parity() ^ 1u)) return;
                 const int a = i0 + (tb.lo(e) & ~1);
-                issue_copy(sm, ring0, rg, j, a, ((i0 + tb.hi(e) + T - a) + 1) & ~1);
+                issue_copy(sm, ring0, rg, j, a, ((i0 + tb.hi(e) + TL - a) + 1) & ~1);
                 rg.next();
             }
         }
@@ -537,6 +552,24 @@ __device__ __forceinline__ bool consume_tile(fold_smem &sm, const fold_table &tb
     return true;
 }
 
+// A tile of `rows` rows (rows <= RL): the variant with exactly that many, straight-line when
+// it has at most 3 live epochs.
+template <int GS, int R, int W, bool KAHAN, int RL>
+__device__ __forceinline__ bool consume_tile_rows(int rows, fold_smem &sm, const fold_table &tb,
+                                                  int g0, int j, int i0, int nE, unsigned use,
+                                                  bool all_used, int nmin, uint32_t mine,
+                                                  best_slots bs, ring &rg) {
+    if constexpr (RL > 1 && GS >= 4) {
+        if (rows < RL)
+            return consume_tile_rows<GS, R, W, KAHAN, RL - 1>(rows, sm, tb, g0, j, i0, nE, use,
+                                                              all_used, nmin, mine, bs, rg);
+    }
+    return nE <= 3 ? consume_tile<GS, RL, W, KAHAN, true>(sm, tb, g0, j, i0, nE, use, all_used,
+                                                          nmin, mine, bs, rg)
+                   : consume_tile<GS, RL, W, KAHAN, false>(sm, tb, g0, j, i0, nE, use, all_used,
+                                                           nmin, mine, bs, rg);
+}
+
 template <int GS, int R, int W, bool KAHAN>
 __device__ void consume_main(fold_smem &sm, uint32_t ring0, best_slots bs, const fold_table &tb,
                              int g0, int nph_sub, ring &rg) {
@@ -557,11 +590,9 @@ __device__ void consume_main(fold_smem &sm, uint32_t ring0, best_slots bs, const
             nE = live_epochs(tb, nE, sm.it.I, i0);
             // (a wait that gave up ends the path at once: the main path has no block barrier,
             // so every thread still meets the caller's next one)
-            const bool ok =
-                nE <= 3 ? consume_tile<GS, R, W, KAHAN, true>(sm, tb, g0, j, i0, nE, use, all_used,
-                                                              nmin, mine, bs, rg)
-                        : consume_tile<GS, R, W, KAHAN, false>(sm, tb, g0, j, i0, nE, use, all_used,
-                                                               nmin, mine, bs, rg);
+            const bool ok = consume_tile_rows<GS, R, W, KAHAN, R>(
+                tile_rows<GS, R>(nph_sub - i0), sm, tb, g0, j, i0, nE, use, all_used, nmin, mine,
+                bs, rg);
             if (!ok) return;
         }
     }
@@ -851,7 +882,7 @@ __device__ __forceinline__ void fold_subgroup_w(fold_smem &sm, uint32_t ring0,
 // (8 -> 4 -> 2 -> 1 periods, as the table allows) in turn; slot g's best key ends in
 // sm.best[g]. A wait that gave up leaves sm.abort set.
 template <bool KAHAN, int R>
-__device__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab, best_slots bs,
+__device__ __forceinline__ void fold_group(fold_smem &sm, unsigned char *raw, unsigned char *tab, best_slots bs,
                            ring &rg) {
     constexpr int T = FT_THREADS * R;
     for (int g0 = 0; g0 < FT_G;) {
