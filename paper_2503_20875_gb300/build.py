@@ -3,7 +3,9 @@
 The translation units compiled in parallel and linked into one shared
 library next to this file:
   csrc/kernels.cu  resample, linear, finalize and batch kernels (nvcc, sm_103a)
-  csrc/fold.cu     the periodic-search fold kernels and launchers (nvcc, sm_103a)
+  csrc/fold.cu     the single-curve fold kernel and its launcher (nvcc, sm_103a)
+  csrc/fold_batch.cu  the batched fold kernel and its launcher (nvcc, sm_103a); both fold
+                   files include the shared device code of csrc/fold.cuh
   csrc/plan.cpp    host planner, FP64 index arithmetic  (g++, -ffp-contract=off)
   csrc/capi.cpp    the C ABI declared in include/cetra.h (g++)
   csrc/noalloc.cu  the allocation-free periodic entry point (nvcc)
@@ -26,7 +28,7 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "fold.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu",
+SOURCES = ["kernels.cu", "fold.cu", "fold_batch.cu", "plan.cpp", "capi.cpp", "noalloc.cu", "batch.cpp", "cnn.cu",
            "neighbours.cu"]
 
 

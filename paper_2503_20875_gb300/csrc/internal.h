@@ -129,6 +129,7 @@ constexpr int FT_THREADS = FT_CWARPS * 32;           // consumer threads
 constexpr int FT_BLOCK = FT_THREADS + 32;            // + the producer warp
 constexpr int FT_T = FT_THREADS * FT_R;              // phases per tile
 constexpr int FT_G = 8;                              // periods per group
+constexpr int FT_PACK_MAXJ = 64;                     // durations a duration-packed item may hold
 constexpr long long FT_WAIT_CYCLES = 2000000000ll;  // ~1 s of SM clocks before a wait gives up
 constexpr uint32_t FT_SUSPEND_NS = 20000;            // suspend hint of one barrier try
 constexpr int FOLD_PAD = FT_STRIP + 16;  // zero cells after each grid row
@@ -138,6 +139,8 @@ constexpr size_t FT_L2_GRID_BYTES = (size_t)64 << 20;
 size_t fold_smem_bytes();
 // Opt the fold kernels in to their dynamic shared memory (fold.cu).
 cudaError_t fold_configure();
+// The same for the batched fold kernels (fold_batch.cu; called by fold_configure).
+cudaError_t batch_fold_configure();
 
 // Device view of one light curve of a batch (cetra_batch_*).
 struct batch_curve {

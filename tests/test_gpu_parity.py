@@ -168,6 +168,30 @@ def test_periods_with_more_epochs_than_the_offset_table():
     assert abs(periods[kb] - P_in) / P_in < 0.01
 
 
+def test_duration_packed_short_periods_in_a_large_launch():
+    """12,000 short trial periods (0.35-3.0 d at a 10-min t0 step: 51-432 phases) over five
+    durations: the launch has more 8-period groups than four per block slot of the GPU, so
+    each work item holds every duration, and the fold packs the phases of several durations
+    into one tile (the duration-packed path) wherever that fills at least half of the lanes;
+    the shortest periods take the epoch-sliced path. Durations longer than a period and a
+    (duration, period) mask leave some durations out of some groups. Every period is compared
+    with the oracle."""
+    periods = synth.log_grid(0.35, 3.0, 12000)
+    w = custom(seed=31, n_points=1296, cadence_s=1800.0, t0_step_s=600.0,
+               durations_h=(1.0, 2.0, 4.0, 8.0, 12.0),
+               planets=[dict(P=1.7, t0=0.6, D=3.0 * HOUR, depth=3e-3, b=0.3)])
+    rng = np.random.default_rng(4)
+    mask = (rng.uniform(size=(periods.size, 5)) < 0.7).astype(np.uint8)
+    g, o = _run_both(w, periods, mask)
+    _check_geometry(g, o)
+    nph = np.ceil(periods / w.t0_step)
+    assert nph.max() <= 448 and periods.size // 8 >= 4 * 2 * 152
+    compare_linear(g, o, w.durations)
+    ps = compare_periodic(g, o, periods)
+    kb = ps["best_k"][0]
+    assert abs(periods[kb] - 1.7) / 1.7 < 0.01
+
+
 def test_host_buffer_api_matches_device_api():
     from paper_2503_20875_gb300 import Context, cetra_linear_search, cetra_periodic_search
     w = custom(seed=6, n_points=5000, cadence_s=120.0, durations_h=(0.5, 1.0, 2.0, 4.0),
