@@ -1,5 +1,7 @@
 // The periodic search of one light curve (Sec. 2.3): fold_kernel and its launcher. The
 // device code it shares with the batched form is in fold.cuh.
+#include <algorithm>
+
 #include "fold.cuh"
 
 namespace {
@@ -79,10 +81,15 @@ cudaError_t launch_fold(cetra_ctx *ctx, const cetra_plan *plan, const float2 *ab
     const int n_groups = (K + FT_G - 1) / FT_G;
     const size_t grid_bytes = (size_t)plan->J * (size_t)plan->ab_ld * sizeof(float2);
     // one duration per work item when the grid exceeds the L2 (the blocks in flight then share
-    // a row), or when whole groups would not give every block slot of the GPU four items
+    // a row); when whole groups would not give every block slot of the GPU FT_ITEMS_PER_SLOT
+    // items, the durations are split into chunks as long as that many items still result
     const int64_t slots = (int64_t)ctx->num_sms * FT_MIN_BLOCKS;
-    const int jchunk =
-        (grid_bytes > FT_L2_GRID_BYTES || (int64_t)n_groups < 4 * slots) ? 1 : plan->J;
+    int jchunk = plan->J;
+    if (grid_bytes > FT_L2_GRID_BYTES)
+        jchunk = 1;
+    else if ((int64_t)n_groups < FT_ITEMS_PER_SLOT * slots)
+        jchunk = (int)std::max<int64_t>(
+            1, (int64_t)n_groups * plan->J / ((int64_t)FT_ITEMS_PER_SLOT * slots));
     const int n_chunks = (plan->J + jchunk - 1) / jchunk;
     const int64_t items = (int64_t)n_groups * n_chunks;
     if (items > 2147483647) return cudaErrorInvalidConfiguration;

@@ -122,6 +122,9 @@ constexpr int LIN_SUB = 16;  // register blocks per partial sum of the linear ke
 #ifndef FT_TAB_BYTES
 #define FT_TAB_BYTES (40 * 1024)  // epoch table: u16 offsets + two int32 per epoch
 #endif
+#ifndef FT_ITEMS_PER_SLOT
+#define FT_ITEMS_PER_SLOT 2  // single-curve launches: work items per block slot at least (a
+#endif                       // launch of fewer groups splits its durations into chunks)
 #ifndef FT_CWARPS
 #define FT_CWARPS 7       // consumer warps per block (+ the producer warp: 8 warps, 128 registers)
 #endif
