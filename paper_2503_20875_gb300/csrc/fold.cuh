@@ -6,8 +6,10 @@
 // pairs over the epoch cells i + o_e, o_e = floor(e P / s + 1/2) (the nearest t0 point of
 // epoch e, FP64). A null window is (0, 0) and drops out of the sums.
 //
-// Work: one block per group of FT_G neighbouring trial periods (and, for grids larger than
-// the L2, per duration). Neighbouring periods read nearly the same cells, so for a tile of
+// Device code shared by the single-curve fold (fold.cu) and the batched fold (fold_batch.cu).
+//
+// Work: one block per group of FT_G neighbouring trial periods and a chunk of durations (one
+// duration for grids larger than the L2). Neighbouring periods read nearly the same cells, so for a tile of
 // T phases and an epoch e the block copies the union of the cells its periods need,
 // [i0 + min_g o_e(g), i0 + max_g o_e(g) + T), into shared memory with one bulk copy and every
 // period reads its cells from there.
@@ -28,8 +30,10 @@
 // table fits, else 16-bit), plus the smallest and largest offset of the epoch (the strip's
 // extent). Groups whose table does not fit, or whose offsets spread wider than a strip
 // allows, are split 8 -> 4 -> 2 -> 1; a single period whose table does not fit is folded
-// straight from global memory. Periods with few phases (at most T/2) fold several epochs per
-// strip (epoch slices).
+// straight from global memory. The last tile of each duration row folds only the rows of
+// FT_THREADS phases that hold a phase. Periods with few phases (at most T/2) fold several
+// durations per tile when the work item has several (duration-packed path), else several
+// epochs per strip (epoch slices).
 //
 // Bounded waits: every barrier wait gives up after FT_WAIT_CYCLES; the thread records
 // CETRA_ETIMEOUT in the status word and raises the block's abort flag, after which no thread
