@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= set(N.SIGNATURES), set(names) - set(N.SIGNATURES)
 
 
+def test_build_compiles_every_source():
+    """Every translation unit under csrc/ is in the build's list (a unit left out would leave
+    its symbols missing from libcetra.so on a fresh machine), and the list names no missing
+    file."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "cetra_build", os.path.join(ROOT, "paper_2503_20875_gb300", "build.py"))
+    build = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(build)
+    units = sorted(f for f in os.listdir(build.CSRC) if f.endswith((".cu", ".cpp", ".c")))
+    assert sorted(build.SOURCES) == units
+
+
 def test_header_is_plain_c(tmp_path):
     """A C99 translation unit that includes the header and takes the address of every
     declared entry point compiles without a warning (the boundary needs no C++)."""
