@@ -847,7 +847,8 @@ def other_configs():
                                   "gpu_launches") if k in d}
         keep["args"] = " ".join(extra)
         keep["config"] = {k: d["config"][k] for k in ("workload", "precision", "n_periods",
-                                                      "n_t0", "n_durations") if k in d["config"]}
+                                                      "n_t0", "n_durations", "fold_variant")
+                          if k in d["config"]}
         if d.get("e2e"):
             keep["e2e"] = {k: d["e2e"].get(k) for k in ("value", "unit", "api")}
         if d.get("roofline"):
